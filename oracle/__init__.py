@@ -1,0 +1,30 @@
+"""Oracle for the compact finite-difference (CFD) hot path of arXiv 2302.14858.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
+restatement of the paper's method (FP64 numpy for the block operators, exact
+rationals / mpmath for scheme design).  Only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import, call or execute anything in it.  The CUDA
+product path (``paper_2302_14858_gb300``) shares no code with it and never
+routes through it.
+
+Modules
+-------
+schemes   Taylor constraints (Sec. "Method", Eq. mdAnsatz / Eq. Tcons), the
+          modified wavenumber (Eq. fdpwerrdef) and its relative error
+          (Eq. relmodnormwavnum), spectral tuning as an equality-constrained
+          quadratic programme (Eqs. sp_error, optfunc, gammacut) and the
+          C_0-matched explicit closures (Eqs. errrelmodwavcent,
+          errelmodwavecentmatch).
+cfd       The block operator: ghost fill (matrix G, Eq. example_G), closed
+          banded solve (Eq. sch_cent_om), hybrid iteration (Eq. iter_center_P),
+          the embedded dense operators (Eqs. diff_mat_subL/R/MR,
+          iter_scheme), 3D application with symmetrised mixed derivatives
+          (Sec. "Z4c: system description"), and classical RK4 for the linear
+          wave system.
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
+the 3D mixed-derivative path with hybrid iteration (``apply3d`` with
+``n_iter > 0`` and a mixed op), whose pin is only partial (tensor-product
+consistency and the iteration fixed point; parity unpinned beyond that).
+"""
