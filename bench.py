@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Throughput of the compact finite-difference hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec P] [--impl ours|reference]
+
+One step = one pass of the whole path over one batch: ghost exchange of all
+fields (matrix G, Eq. example_G), then all requested derivative ops of every
+field on every MeshBlock (closed block systems, Eq. sch_cent_om, plus the
+hybrid iteration, Eq. iter_center_P, on uniform meshes).  Metric: Gpoint-ops/s
+= interior points x fields x ops / step time.  Prints ONE JSON line (rank 0).
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path has no data exchange between replicas), value = units of all
+ranks / max-over-ranks time ("weak" scaling).  --impl reference times the
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoint-ops/s: split-BF16 TC CFD vs FP64 banded solve, err ≤1e-6 vs FP64"
+L2_BYTES = 129 * 2 ** 20
+FP64_NOMINAL_GFLOPS = 1250.0      # GB300 FP64 (non-tensor) nominal, profiling recipe table
+
+PREC = {"fp64_banded": 0, "tc_bf16x3": 1, "tc_bf16_exact": 2, "tc_tf32": 3}
+DTYPE_NAME = {0: "f64", 1: "f64", 2: "f64", 3: "f64"}
+
+WORKLOADS = {
+    # 128^3 periodic, 512 blocks of 16^3, 4 FP64 fields, 9 ops, one hybrid iteration
+    "cfd128_b16_f4_fp64": dict(kind="uniform", NM=128, N=16, nf=4, fields=2, dtype="f64", n_iter=1),
+    # 256^3 periodic, 512 blocks of 32^3, 4 FP64 fields, 9 ops, one hybrid iteration
+    "cfd256_b32_f4_fp64": dict(kind="uniform", NM=256, N=32, nf=4, fields=3, dtype="f64", n_iter=1),
+    # 448 blocks 16^3 + 64 blocks 32^3, 22 FP32 fields, 9 ops, closures only
+    "box448x16_64x32_f22_fp32": dict(kind="boxinbox", nf=22, fields=4, dtype="f32", n_iter=0),
+}
+DEFAULT_WORKLOAD = "cfd128_b16_f4_fp64"
+
+
+def scheme_descs():
+    """Tuned (Q^1_3[eta_c=1], Tabs. num_deg_one/two) interior schemes as the paper prints them.
+
+    The closures are built by the library (C_0 matching, closure=NULL).
+    """
+    d1 = {"deriv": 1, "order": 6, "a": 0.37987923,
+          "rhs": [0.0023272948, -0.052602255, -0.78165660, 0.0, 0.78165660, 0.052602255, -0.0023272948]}
+    d2 = {"deriv": 2, "order": 6, "a": 0.24246603,
+          "rhs": [-0.0037062571, 0.14095923, 0.95445144, -2.1834088, 0.95445144, 0.14095923, -0.0037062571]}
+    return d1, d2
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                p = [v.strip() for v in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = float(p[2])
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workloads
+
+
+def build_workload(name, dev, torch):
+    from paper_2302_14858_gb300 import workloads as W
+    spec = WORKLOADS[name]
+    if spec["kind"] == "uniform":
+        mesh = W.uniform_mesh(spec["NM"], spec["N"], 4)
+    else:
+        mesh = W.box_in_box_mesh(4)
+    cfgid = spec["fields"]
+    funcs = W.workload_fields(cfgid)[: spec["nf"]]
+    tdt = torch.float64 if spec["dtype"] == "f64" else torch.float32
+    # evaluate the analytic fields on the device, block by block (same formulas as workloads.sample)
+    parts = []
+    for b in range(mesh.nblocks):
+        xs = [torch.as_tensor(c, device=dev, dtype=torch.float64) for c in mesh.coords(b)]
+        Z, Y, X = torch.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+        vals = []
+        for f in funcs:
+            vals.append(_eval_torch(f, X, Y, Z, torch).to(tdt))
+        parts.append(torch.stack(vals).reshape(-1))
+    fields = torch.cat(parts)
+    return spec, mesh, fields
+
+
+def _eval_torch(f, X, Y, Z, torch):
+    from paper_2302_14858_gb300 import workloads as W
+    if isinstance(f, W.SineSum):
+        out = torch.zeros_like(X)
+        for (kx, ky, kz), A, p in zip(f.k, f.A, f.phi):
+            out += float(A) * torch.sin(float(kx) * X + float(ky) * Y + float(kz) * Z + float(p))
+        return out
+    if isinstance(f, W.PeriodicGaussian):
+        out = torch.zeros_like(X)
+        for sz in (-1, 0, 1):
+            for sy in (-1, 0, 1):
+                for sx in (-1, 0, 1):
+                    r2 = ((X - f.c[0] - sx * W.TWO_PI) ** 2 + (Y - f.c[1] - sy * W.TWO_PI) ** 2
+                          + (Z - f.c[2] - sz * W.TWO_PI) ** 2)
+                    out += torch.exp(-r2 / (2.0 * f.sigma ** 2))
+        return out
+    if isinstance(f, W.InverseDistance):
+        out = torch.zeros_like(X)
+        for c in f.centers:
+            d2 = torch.zeros_like(X)
+            for v, cc in zip((X, Y, Z), c):
+                dv = torch.remainder(torch.abs(v - float(cc)), W.TWO_PI)
+                dv = torch.minimum(dv, W.TWO_PI - dv)
+                d2 += dv * dv
+            out += 1.0 / (torch.sqrt(d2) + 0.5)
+        return out
+    if isinstance(f, W.Sum):
+        out = torch.zeros_like(X)
+        for p in f.parts:
+            out += _eval_torch(p, X, Y, Z, torch)
+        return out
+    raise TypeError(type(f))
+
+
+# ------------------------------------------------------------------ algorithmic work
+
+
+def banded_flops_per_step(mesh, nf, mask_ops, n_iter, M=3, h=4, g=4):
+    """FP64 flops of the banded path (RHS FMA chains + Thomas sweeps) for one apply."""
+    def closed(N, pencils):
+        rows_int, rows_clo = N - 2, 2
+        rhs = rows_int * (2 * (2 * M + 1) - 1) + rows_clo * (2 * (2 * h + 1) - 1)
+        return pencils * (rhs + N + 1 + 3 * (N - 1) + 2 * (N - 1))
+
+    def iterated(N, pencils):
+        rows = N + 2
+        return pencils * (rows * (2 * (2 * M + 1) - 1) + rows + 3 * (N + 3) + 2 * (N + 1))
+
+    def stage(N, pencils):
+        return closed(N, pencils) + n_iter * iterated(N, pencils)
+
+    total = 0
+    for b in range(mesh.nblocks):
+        N = int(mesh.n[b])
+        E = N + 2 * g
+        for op in mask_ops:
+            if len(op) == 2 or op[1] == op[2]:
+                total += stage(N, N * N)
+            else:
+                total += 2 * (stage(N, E * N) + stage(N, N * N)) + 2 * N ** 3
+    return total * nf
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+
+
+def cpu_baseline(spec, seconds=12.0):
+    """Time the oracle on a bounded sample of the workload (host cores)."""
+    from oracle import cfd as C
+    from paper_2302_14858_gb300 import workloads as W
+    with open(os.path.join(ROOT, "tests", "golden", "schemes.json")) as fh:
+        S = json.load(fh)
+    e1, e2 = S["Q13_1_d1"], S["Q13_1_d2"]
+    s1 = C.Sch(1, e1["a"], tuple(e1["rhs"]), tuple(e1["closure"]))
+    s2 = C.Sch(2, e2["a"], tuple(e2["rhs"]), tuple(e2["closure"]))
+    g = 4
+    if spec["kind"] == "uniform":
+        NM, N = spec["NM"], spec["N"]
+        # sample: one field on a (NM/2)^3 periodic sub-problem with the same block size
+        NS = max(2 * N, NM // 2)
+        f = W.workload_fields(spec["fields"])[0]
+        dx = 2 * np.pi / NS
+        x = (np.arange(NS) + 0.5) * dx
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        ext = C.ghost_fill_3d(f(X, Y, Z), N, g)
+        units = 0
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            C.apply_uniform(ext, s1, s2, (dx, dx, dx), N, g, C.OPS, spec["n_iter"])
+            units += NS ** 3 * 9
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        el = time.perf_counter() - t0
+        sample = f"oracle apply_uniform, 1 field, {NS}^3 as {(NS // N) ** 3} blocks of {N}^3, 9 ops, " \
+                 f"n_iter={spec['n_iter']}, {reps} reps"
+    else:
+        mesh = W.box_in_box_mesh(g)
+        f = W.workload_fields(4)[0]
+        rng = np.random.default_rng(0)
+        blocks = list(rng.choice(mesh.nblocks, size=16, replace=False))
+        data = W.sample(mesh, [f], blocks=blocks)
+        units, reps = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            for b, arr in zip(blocks, data):
+                N = int(mesh.n[b])
+                C.apply_block(arr[0], s1, s2, mesh.dx[b], N, g, C.OPS)
+                units += N ** 3 * 9
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        el = time.perf_counter() - t0
+        sample = f"oracle apply_block on 16 random blocks (both sizes), 1 field, 9 ops, {reps} reps"
+    return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
+# ------------------------------------------------------------------ main
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp64_banded", choices=sorted(PREC))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-iter", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    spec = dict(WORKLOADS[args.workload])
+    if args.n_iter is not None:
+        spec["n_iter"] = args.n_iter
+
+    if args.impl == "reference":
+        return run_reference(args, spec, rank)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2302_14858_gb300 import cfd
+    d1, d2 = scheme_descs()
+    scheme = cfd.cfd_scheme_create(d1, d2)
+    spec_, mesh, fields = build_workload(args.workload, dev, torch)
+    dtype = cfd.CFD_F64 if spec["dtype"] == "f64" else cfd.CFD_F32
+    blocks = cfd.cfd_blocks_bind(scheme, mesh.n, mesh.dx, mesh.neighbors, mesh.g, dtype)
+    nf = spec["nf"]
+    mask = cfd.CFD_OP_ALL
+    nops = 9
+    prec = PREC[args.prec]
+    n_iter = spec["n_iter"]
+    nint = int(sum(int(n) ** 3 for n in mesh.n))
+    out = torch.empty(nint * nf * nops, dtype=fields.dtype, device=dev)
+    ws = cfd.cfd_apply_workspace(blocks, nf, mask, prec, n_iter)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        cfd.cfd_exchange_ghosts(blocks, fields, nf, stream)
+        cfd.cfd_apply(blocks, fields, nf, mask, prec, n_iter, out, work, stream)
+
+    for _ in range(args.warmup):
+        step()
+    cfd.cfd_sync_status(blocks, stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    launches0 = cfd.cfd_kernel_launches()
+    cfd.cfd_profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    cfd.cfd_sync_status(blocks, stream)
+    ms_total = ev0.elapsed_time(ev1)
+    launches = cfd.cfd_kernel_launches() - launches0
+    prof = {name: cfd.cfd_profile_read(fid) for name, fid in cfd.KERNEL_FAMILIES.items()}
+    cfd.cfd_profile_enable(False)
+
+    ms_step = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    units = nint * nf * nops
+    value = units * world / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel
+    fam, (nl, tl) = max(prof.items(), key=lambda kv: kv[1][1])
+    if fam == "line":
+        fl = banded_flops_per_step(mesh, nf, cfd.OPS, n_iter) * args.steps
+        achieved = fl / (tl * 1e-3) / 1e9
+        roof = {"kernel": "k_line (FP64 banded pencil solve)", "bound": "alu", "achieved": round(achieved, 2),
+                "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s", "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table)",
+                "launches_per_step": nl / args.steps, "avg_launch_ms": tl / max(nl, 1),
+                "share_of_step": round(tl / ms_total, 4), "traffic": None}
+    else:
+        roof = {"kernel": fam, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                "traffic": None}
+
+    # end-to-end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty(fields.numel(), dtype=fields.dtype, pin_memory=True)
+        host_in.copy_(fields)
+        host_out = torch.empty(out.numel(), dtype=out.dtype, pin_memory=True)
+        for _ in range(2):
+            fields.copy_(host_in, non_blocking=True)
+            step()
+            host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        ke = max(3, args.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(ke):
+            fields.copy_(host_in, non_blocking=True)
+            step()
+            host_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / ke
+        e2e = {"value": round(units * world / (ms_e2e * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s",
+               "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+               "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
+               "ms_per_step": round(ms_e2e, 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec)
+
+    if rank == 0:
+        in_bytes = fields.numel() * fields.element_size()
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gpoint-ops/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": spec["dtype"], "data": "synthetic (seeded analytic fields)",
+            "config": {"workload": args.workload, "path": args.prec, "n_iter": n_iter, "fields": nf, "ops": nops,
+                       "blocks": mesh.nblocks, "points_per_field": nint,
+                       "l2": "inputs larger than L2" if in_bytes > L2_BYTES else "inputs fit L2",
+                       "input_bytes": in_bytes, "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args, spec, rank):
+    """The oracle as the reference arm, on host cores, same metric and config."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(spec, seconds=0.5)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(spec, seconds=2.0))
+    el = time.perf_counter() - t0
+    v = statistics.median(r["value"] for r in vals)
+    line = {"metric": METRIC, "value": round(v, 6), "unit": "Gpoint-ops/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded analytic fields)", "impl": "reference",
+            "config": {"workload": args.workload, "path": "oracle (numpy FP64, host)", "n_iter": spec["n_iter"]},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": round(v, 6), "unit": "Gpoint-ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * cfd.h -- C ABI of the GB300 compact finite-difference (CFD) operator library.
+ *
+ * The library applies centred, tridiagonal compact finite-difference schemes
+ * (arXiv 2302.14858, Eq. mdAnsatz with alpha^{(d)} = (a, 1, a)) to 3D fields
+ * split into MeshBlocks with ghost layers.  Each block solves its own banded
+ * system closed by explicit, error-matched closures (Eq. sch_cent_om), with
+ * optional hybrid matching-communication iterations (Eq. iter_center_P).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All entry points return a cfd_status; nothing aborts or throws across
+ *    the ABI.  cfd_last_error() gives a message for the last failure on the
+ *    calling thread.
+ *  - Host pointers (coefficients, tables) are read during the call and not
+ *    retained.  Device pointers (fields, outputs, workspaces) are owned by the
+ *    caller and must stay valid until the work queued on `stream` finishes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is asynchronous; errors detected on the device
+ *    (bounded waits that ran out, failed self-checks) are latched in a status
+ *    word of the blocks handle and reported by cfd_sync_status().
+ *  - Field layout (device memory): blocks in bind order; block b holds
+ *    nfields arrays of (N_b + 2 ng)^3 values, axes (z, y, x), x fastest.
+ *    Interior index k = 0..N_b-1 of an axis sits at array index k + ng
+ *    (cell-centred sampling, Eq. gridDisc CC).
+ *  - Output layout: blocks in bind order; block b holds nfields x nops arrays
+ *    of N_b^3 interior values (z, y, x), ops in increasing bit order of
+ *    op_mask.  Outputs have the field dtype.
+ */
+#ifndef CFD_H
+#define CFD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cfd_status {
+  CFD_OK = 0,
+  CFD_ERR_ARG = 1,            /* invalid argument (null pointer, size, layout) */
+  CFD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  CFD_ERR_UNSUPPORTED = 3,    /* valid request outside what this build supports */
+  CFD_ERR_NOT_CONVERGED = 4,  /* reserved: iteration did not reach a tolerance */
+  CFD_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
+  CFD_ERR_DEVICE_ASSERT = 6,  /* a device-side self-check failed */
+  CFD_ERR_ALLOC = 7           /* host or device allocation failed */
+} cfd_status;
+
+/* Arithmetic of cfd_apply. */
+typedef enum cfd_precision {
+  CFD_FP64_BANDED = 0,   /* FP64 right-hand side + Thomas solve per pencil */
+  CFD_TC_BF16X3 = 1,     /* dense D = A^-1 B on BF16 tensor cores, hi/lo split, 3 products */
+  CFD_TC_BF16_EXACT = 2, /* dense D on BF16 tensor cores, exact integer slices (FP64-level result) */
+  CFD_TC_TF32 = 3        /* dense D on TF32 tensor cores, one product */
+} cfd_precision;
+
+typedef enum cfd_dtype { CFD_F64 = 0, CFD_F32 = 1 } cfd_dtype;
+
+/* Derivative outputs (op_mask bits). Mixed ops are symmetrised (D_i D_j + D_j D_i)/2. */
+#define CFD_OP_DX  (1u << 0)
+#define CFD_OP_DY  (1u << 1)
+#define CFD_OP_DZ  (1u << 2)
+#define CFD_OP_DXX (1u << 3)
+#define CFD_OP_DYY (1u << 4)
+#define CFD_OP_DZZ (1u << 5)
+#define CFD_OP_DXY (1u << 6)
+#define CFD_OP_DXZ (1u << 7)
+#define CFD_OP_DYZ (1u << 8)
+#define CFD_OP_ALL 0x1FFu
+
+/* Neighbour direction r of block b: (dz, dy, dx) in {-1,0,1}^3 without the
+ * centre, lexicographic with dz slowest: r = 9(dz+1) + 3(dy+1) + (dx+1),
+ * minus one when that exceeds 13. */
+#define CFD_NDIRS 26
+
+/*
+ * One centred tridiagonal compact scheme of derivative degree `deriv`
+ * (Eq. mdAnsatz with alpha^{(d)} = (lhs_offdiag, 1, lhs_offdiag) and
+ * alpha^{(0)}_{-M..M}), together with its explicit closure C-bar_{p+1}
+ * (Eq. sch_cent_om rows k = k*_+-), e.g. the appendix tables pade_deg_one,
+ * pade_deg_two, num_deg_one and num_deg_two.
+ *   order             formal order 2p of the interior scheme (4, 6, 8 or 10).
+ *   M                 half-width of the interior right-hand side, 1 <= M <= 5.
+ *   rhs               2M+1 host values alpha^{(0)}_{-M..M}.
+ *   closure_halfwidth p+1, 2 <= p+1 <= 6 (ignored when closure is NULL).
+ *   closure           2(p+1)+1 host values, or NULL: the library then builds
+ *                     the closure of half-width order/2 + 1 whose eta^{2p}
+ *                     error constant matches the interior's C_0 and whose
+ *                     eta^{2p+1} term vanishes (the two conditions after
+ *                     Eq. errelmodwavecentmatch).
+ */
+typedef struct cfd_scheme_desc {
+  int deriv;
+  int order;
+  int M;
+  double lhs_offdiag;
+  const double *rhs;
+  int closure_halfwidth;
+  const double *closure;
+} cfd_scheme_desc;
+
+typedef struct cfd_scheme_s *cfd_scheme_t;
+typedef struct cfd_blocks_s *cfd_blocks_t;
+
+/*
+ * Create a scheme pair: `first` (deriv = 1) for d_x, d_y, d_z and the mixed
+ * ops, `second` (deriv = 2) for d_xx, d_yy, d_zz.  Either may be NULL if the
+ * ops that need it are never requested.  Host-only; allocates host memory.
+ * Errors: CFD_ERR_ARG (bad degree, widths, or a non-diagonally-dominant
+ * system 2|a| >= 1), CFD_ERR_ALLOC.
+ */
+cfd_status cfd_scheme_create(const cfd_scheme_desc *first, const cfd_scheme_desc *second,
+                             cfd_scheme_t *out);
+
+/* Copy the closure in use for degree `deriv` (built or given) to `closure`
+ * (room for 13 doubles); *halfwidth receives p+1. */
+cfd_status cfd_scheme_closure(cfd_scheme_t scheme, int deriv, double *closure, int *halfwidth);
+
+void cfd_scheme_destroy(cfd_scheme_t scheme);
+
+/*
+ * Bind a set of MeshBlocks (Sec. "Domain decomposition"; the communication
+ * pattern of matrix G, Eq. example_G) to a scheme on the current CUDA device.
+ *   nblocks    number of blocks, >= 1.
+ *   block_n    host [nblocks]: interior points per axis N_b, 8 <= N_b <= 32,
+ *              N_b >= ng.
+ *   dx         host [nblocks][3]: grid spacing (dx, dy, dz) of each block.
+ *   neighbors  host [nblocks][26]: neighbour block per direction (see
+ *              CFD_NDIRS), -1 = the caller fills that ghost region itself
+ *              (e.g. an interface to a block of another size).  A neighbour
+ *              must have the same N as the block.  A block that is its own
+ *              neighbour on both faces of an axis covers the whole periodic
+ *              line: that axis uses the undecomposed cyclic scheme.
+ *   ng         ghost layers, >= closure half-width and >= M + 1.
+ *   dtype      CFD_F64 or CFD_F32 fields.
+ * Builds per block size: the banded LU factors of the closed and iterated
+ * systems and the dense operators D = A^-1 B ([0]D of Eq. iter_scheme) with
+ * their tensor-core copies; uploads them with the neighbour tables.
+ * Allocates device memory owned by the handle.
+ */
+cfd_status cfd_blocks_bind(cfd_scheme_t scheme, int nblocks, const int *block_n, const double *dx,
+                           const int *neighbors, int ng, cfd_dtype dtype, cfd_blocks_t *out);
+
+void cfd_blocks_destroy(cfd_blocks_t blocks);
+
+/*
+ * Ghost exchange (matrix G of Eq. example_G): for every block and every
+ * direction with a neighbour >= 0, copy the neighbour's interior slab into
+ * the block's ghost region (faces, edges and corners).  `fields` is the
+ * device field buffer described above with `nfields` fields.  Exact copy.
+ */
+cfd_status cfd_exchange_ghosts(cfd_blocks_t blocks, void *fields, int nfields, void *stream);
+
+/* Device workspace cfd_apply needs for this request (bytes, 256-aligned). */
+cfd_status cfd_apply_workspace(cfd_blocks_t blocks, int nfields, unsigned op_mask, cfd_precision prec,
+                               int n_iter, size_t *bytes);
+
+/*
+ * Derivatives of ghost-filled fields.  For every block, field and op in
+ * `op_mask`: d_i with the first-degree scheme, d_ii with the second-degree
+ * scheme, d_ij (i != j) as (D_i[D_j f] + D_j[D_i f]) / 2 where the inner D_j
+ * is evaluated on the ghost rows of axis i too (needs edge ghosts).
+ *   n_iter     hybrid iterations (Eq. iter_center_P), 0 = closures only.
+ *              n_iter > 0 needs same-size face neighbours on every
+ *              decomposed axis.
+ *   prec       arithmetic (see cfd_precision).
+ *   work       device workspace of at least cfd_apply_workspace() bytes.
+ * Errors: CFD_ERR_ARG, CFD_ERR_UNSUPPORTED, CFD_ERR_CUDA.
+ */
+cfd_status cfd_apply(cfd_blocks_t blocks, const void *fields, int nfields, unsigned op_mask,
+                     cfd_precision prec, int n_iter, void *out, void *work, size_t work_bytes,
+                     void *stream);
+
+/* Device workspace of cfd_wave_rk_step (bytes). */
+cfd_status cfd_wave_workspace(cfd_blocks_t blocks, cfd_precision prec, int n_iter, size_t *bytes);
+
+/*
+ * One classical RK4 step (ERK4 of Sec. "Two dimensional advection", fully
+ * discrete) of the linear wave system d/dt Phi = K, d/dt K = sum_i D2_i Phi
+ * (Eq. toyShiftWaveEqnSys with zero shift).  `phi` and `K` are single-field
+ * buffers in the field layout; ghosts of Phi are exchanged before every
+ * stage (blocks with -1 neighbours are not supported here).  Needs the
+ * second-degree scheme.
+ */
+cfd_status cfd_wave_rk_step(cfd_blocks_t blocks, void *phi, void *K, double dt, cfd_precision prec,
+                            int n_iter, void *work, size_t work_bytes, void *stream);
+
+/* Wait for `stream`, then read and clear the device status word of the
+ * handle: CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_DEVICE_ASSERT. */
+cfd_status cfd_sync_status(cfd_blocks_t blocks, void *stream);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *cfd_last_error(void);
+
+/*
+ * Diagnostics (no counterpart in the paper).  Kernel families:
+ * 0 ghost exchange, 1 banded line solve, 2 RK4 combine, 3 dense tensor-core
+ * operator, 4 dense halo rows.  cfd_kernel_launches() counts every kernel the
+ * library has launched in this process.  With profiling on, every launch is
+ * bracketed by CUDA events recorded on its own stream; cfd_profile_read()
+ * (after the stream has finished) returns the number of launches and their
+ * summed device time for one family since profiling was last enabled.
+ * cfd_profile_enable(0) stops recording; enabling resets the sums.
+ */
+unsigned long long cfd_kernel_launches(void);
+cfd_status cfd_profile_enable(int on);
+cfd_status cfd_profile_read(int family, unsigned long long *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFD_H */

@@ -1,0 +1,245 @@
+"""Thin ctypes binding of the C ABI in include/cfd.h (argument marshalling only).
+
+Every function keeps the C name and forwards to libcfd.so; all arithmetic
+runs in the library's CUDA kernels.  Device buffers are passed as torch
+tensors (or raw integer addresses); streams as torch.cuda.Stream, an integer
+cudaStream_t, or None for the current torch stream.  A failed call raises
+``CfdError`` carrying the status and the library's message.  Importing this
+module fails loudly when libcfd.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_size_t, c_uint, c_void_p
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcfd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2302_14858_gb300.build` "
+        "(the CFD operators have no other implementation)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes
+CFD_OK, CFD_ERR_ARG, CFD_ERR_CUDA, CFD_ERR_UNSUPPORTED, CFD_ERR_NOT_CONVERGED, CFD_ERR_TIMEOUT, \
+    CFD_ERR_DEVICE_ASSERT, CFD_ERR_ALLOC = range(8)
+# precisions
+CFD_FP64_BANDED, CFD_TC_BF16X3, CFD_TC_BF16_EXACT, CFD_TC_TF32 = range(4)
+# dtypes
+CFD_F64, CFD_F32 = 0, 1
+# ops
+OPS = ("dx", "dy", "dz", "dxx", "dyy", "dzz", "dxy", "dxz", "dyz")
+OP_BITS = {name: 1 << i for i, name in enumerate(OPS)}
+CFD_OP_ALL = 0x1FF
+
+EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd_blocks_bind",
+           "cfd_blocks_destroy", "cfd_exchange_ghosts", "cfd_apply_workspace", "cfd_apply",
+           "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_sync_status", "cfd_last_error",
+           "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read")
+KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4}
+
+
+class CfdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cfd status {status}: {msg}")
+        self.status = status
+
+
+class SchemeDesc(ctypes.Structure):
+    _fields_ = [("deriv", c_int), ("order", c_int), ("M", c_int), ("lhs_offdiag", c_double),
+                ("rhs", POINTER(c_double)), ("closure_halfwidth", c_int), ("closure", POINTER(c_double))]
+
+
+_lib.cfd_scheme_create.argtypes = [POINTER(SchemeDesc), POINTER(SchemeDesc), POINTER(c_void_p)]
+_lib.cfd_scheme_create.restype = c_int
+_lib.cfd_scheme_closure.argtypes = [c_void_p, c_int, POINTER(c_double), POINTER(c_int)]
+_lib.cfd_scheme_closure.restype = c_int
+_lib.cfd_scheme_destroy.argtypes = [c_void_p]
+_lib.cfd_scheme_destroy.restype = None
+_lib.cfd_blocks_bind.argtypes = [c_void_p, c_int, POINTER(c_int), POINTER(c_double), POINTER(c_int), c_int, c_int,
+                                 POINTER(c_void_p)]
+_lib.cfd_blocks_bind.restype = c_int
+_lib.cfd_blocks_destroy.argtypes = [c_void_p]
+_lib.cfd_blocks_destroy.restype = None
+_lib.cfd_exchange_ghosts.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
+_lib.cfd_exchange_ghosts.restype = c_int
+_lib.cfd_apply_workspace.argtypes = [c_void_p, c_int, c_uint, c_int, c_int, POINTER(c_size_t)]
+_lib.cfd_apply_workspace.restype = c_int
+_lib.cfd_apply.argtypes = [c_void_p, c_void_p, c_int, c_uint, c_int, c_int, c_void_p, c_void_p, c_size_t, c_void_p]
+_lib.cfd_apply.restype = c_int
+_lib.cfd_wave_workspace.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
+_lib.cfd_wave_workspace.restype = c_int
+_lib.cfd_wave_rk_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_size_t, c_void_p]
+_lib.cfd_wave_rk_step.restype = c_int
+_lib.cfd_sync_status.argtypes = [c_void_p, c_void_p]
+_lib.cfd_sync_status.restype = c_int
+_lib.cfd_kernel_launches.argtypes = []
+_lib.cfd_kernel_launches.restype = ctypes.c_ulonglong
+_lib.cfd_profile_enable.argtypes = [c_int]
+_lib.cfd_profile_enable.restype = c_int
+_lib.cfd_profile_read.argtypes = [c_int, POINTER(ctypes.c_ulonglong), POINTER(c_double)]
+_lib.cfd_profile_read.restype = c_int
+_lib.cfd_last_error.argtypes = []
+_lib.cfd_last_error.restype = ctypes.c_char_p
+
+
+def cfd_last_error() -> str:
+    return _lib.cfd_last_error().decode()
+
+
+def _check(status: int):
+    if status != CFD_OK:
+        raise CfdError(status, cfd_last_error())
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class Scheme:
+    """Owning wrapper of cfd_scheme_t."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.cfd_scheme_destroy(self.handle)
+            self.handle = None
+
+
+class Blocks:
+    """Owning wrapper of cfd_blocks_t."""
+
+    def __init__(self, handle: int, nblocks: int, block_n, ng: int, dtype: int):
+        self.handle = handle
+        self.nblocks = nblocks
+        self.block_n = list(block_n)
+        self.ng = ng
+        self.dtype = dtype
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.cfd_blocks_destroy(self.handle)
+            self.handle = None
+
+
+def _desc(d) -> Optional[SchemeDesc]:
+    if d is None:
+        return None
+    rhs = (c_double * len(d["rhs"]))(*d["rhs"])
+    clo = None
+    if d.get("closure") is not None:
+        clo = (c_double * len(d["closure"]))(*d["closure"])
+    M = (len(d["rhs"]) - 1) // 2
+    h = (len(d["closure"]) - 1) // 2 if clo is not None else 0
+    s = SchemeDesc(d["deriv"], d["order"], M, float(d["a"]), ctypes.cast(rhs, POINTER(c_double)), h,
+                   ctypes.cast(clo, POINTER(c_double)) if clo is not None else None)
+    s._keep = (rhs, clo)
+    return s
+
+
+def cfd_scheme_create(first: Optional[dict], second: Optional[dict]) -> Scheme:
+    """Scheme pair from dicts {deriv, order, a, rhs, closure (optional)}."""
+    d1, d2 = _desc(first), _desc(second)
+    h = c_void_p()
+    _check(_lib.cfd_scheme_create(ctypes.byref(d1) if d1 else None, ctypes.byref(d2) if d2 else None,
+                                  ctypes.byref(h)))
+    return Scheme(h.value, (d1, d2))
+
+
+def cfd_scheme_closure(scheme: Scheme, deriv: int):
+    buf = (c_double * 13)()
+    hw = c_int()
+    _check(_lib.cfd_scheme_closure(scheme.handle, deriv, buf, ctypes.byref(hw)))
+    return [buf[i] for i in range(2 * hw.value + 1)]
+
+
+def cfd_blocks_bind(scheme: Scheme, block_n: Sequence[int], dx, neighbors, ng: int, dtype: int) -> Blocks:
+    import numpy as np
+    nb = len(block_n)
+    n_arr = (c_int * nb)(*[int(v) for v in block_n])
+    dx = np.ascontiguousarray(dx, dtype=np.float64).reshape(nb, 3)
+    nbr = np.ascontiguousarray(neighbors, dtype=np.int32).reshape(nb, 26)
+    h = c_void_p()
+    _check(_lib.cfd_blocks_bind(scheme.handle, nb, n_arr, dx.ctypes.data_as(POINTER(c_double)),
+                                nbr.ctypes.data_as(POINTER(c_int)), ng, dtype, ctypes.byref(h)))
+    return Blocks(h.value, nb, block_n, ng, dtype)
+
+
+def cfd_exchange_ghosts(blocks: Blocks, fields, nfields: int, stream=None):
+    _check(_lib.cfd_exchange_ghosts(blocks.handle, _ptr(fields), nfields, _stream(stream)))
+
+
+def cfd_apply_workspace(blocks: Blocks, nfields: int, op_mask: int, prec: int, n_iter: int) -> int:
+    n = c_size_t()
+    _check(_lib.cfd_apply_workspace(blocks.handle, nfields, op_mask, prec, n_iter, ctypes.byref(n)))
+    return n.value
+
+
+def cfd_apply(blocks: Blocks, fields, nfields: int, op_mask: int, prec: int, n_iter: int, out, work,
+              stream=None):
+    nbytes = 0 if work is None else (work.numel() * work.element_size() if hasattr(work, "numel") else 1 << 62)
+    _check(_lib.cfd_apply(blocks.handle, _ptr(fields), nfields, op_mask, prec, n_iter, _ptr(out), _ptr(work),
+                          nbytes, _stream(stream)))
+
+
+def cfd_wave_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
+    n = c_size_t()
+    _check(_lib.cfd_wave_workspace(blocks.handle, prec, n_iter, ctypes.byref(n)))
+    return n.value
+
+
+def cfd_wave_rk_step(blocks: Blocks, phi, K, dt: float, prec: int, n_iter: int, work, stream=None):
+    nbytes = work.numel() * work.element_size()
+    _check(_lib.cfd_wave_rk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), prec, n_iter, _ptr(work), nbytes,
+                                 _stream(stream)))
+
+
+def cfd_sync_status(blocks: Blocks, stream=None):
+    _check(_lib.cfd_sync_status(blocks.handle, _stream(stream)))
+
+
+def cfd_kernel_launches() -> int:
+    return int(_lib.cfd_kernel_launches())
+
+
+def cfd_profile_enable(on: bool):
+    _check(_lib.cfd_profile_enable(1 if on else 0))
+
+
+def cfd_profile_read(family: int):
+    """(launches, summed device ms) of one kernel family since profiling was enabled."""
+    n = ctypes.c_ulonglong()
+    ms = c_double()
+    _check(_lib.cfd_profile_read(family, ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def op_mask(ops: Sequence[str]) -> int:
+    m = 0
+    for o in ops:
+        m |= OP_BITS[o]
+    return m
+
+
+def ops_in_mask(mask: int):
+    return [o for o in OPS if mask & OP_BITS[o]]

@@ -1,0 +1,124 @@
+// Internal structures of the CFD library (host API <-> CUDA kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cfd.h"
+
+namespace cfd {
+
+constexpr int kMaxN = 32;        // largest block interior size
+constexpr int kMaxM = 5;         // largest interior half-width
+constexpr int kMaxH = 6;         // largest closure half-width
+constexpr int kMaxIter = kMaxN + 4;
+
+// Coefficients of one centred tridiagonal scheme (host copy).
+struct SchemeCoef {
+  bool present = false;
+  int d = 0, order = 0, M = 0, h = 0;
+  double a = 0.0;
+  double rhs[2 * kMaxM + 1] = {};
+  double clo[2 * kMaxH + 1] = {};
+};
+
+// Everything one pencil solve needs for one (block size N, degree d).
+// Passed to kernels by value.
+struct LineTables {
+  int N, M, h, d;
+  double a;
+  double rhs[2 * kMaxM + 1];
+  double clo[2 * kMaxH + 1];
+  // Closed system of Eq. sch_cent_om, rows k = 0..N-1 (Thomas factors):
+  //   forward  y_k = (r_k - lo_k y_{k-1}) * inv_k,  back  x_k = y_k - c_k x_{k+1}.
+  double lo[kMaxN], c[kMaxN], inv[kMaxN];
+  // Iterated system of Eq. iter_center_P, rows k = -2..N+1 stored at k + 2.
+  double ilo[kMaxIter], ic[kMaxIter], iinv[kMaxIter];
+  // Cyclic (undecomposed periodic) system by Sherman-Morrison: Thomas factors
+  // of the corner-modified tridiagonal T, the solution z of T z = u and
+  // 1/(1 + v.z); x = y - (y_0 - a y_{N-1}) * vfac * z.
+  double ylo[kMaxN], yc[kMaxN], yinv[kMaxN], z[kMaxN];
+  double vfac;
+};
+
+// One axis-solve stage over a group of same-size blocks.
+struct LineParams {
+  const void *in;          // field buffer or scratch (double)
+  void *out;               // output buffer, scratch or nothing (halo-only pass)
+  const int *blocks;       // [nblk] global block ids of this group
+  const long long *extpre; // [nblocks] sum over previous blocks of E^3
+  const long long *intpre; // [nblocks] sum over previous blocks of N^3
+  const int *nbr;          // [nblocks][26]
+  const double *scale;     // [nblocks][2][3] 1/dx^d per degree, axis (x, y, z)
+  const double *halo_in;   // [nblocks][nf][P][2] values exported by neighbours
+  double *halo_out;
+  int nblk, nf, nops, opidx;
+  int g;
+  int in_field;            // 1: in is the field buffer (dtype), 0: double scratch
+  int out_mode;            // 0 store final, 1 average into final, 2 store scratch, 3 halo only
+  int axis;                // 0 z, 1 y, 2 x (box axis order)
+  int t1, t2;              // transverse box axes (t2 fastest)
+  int in_dims[3], out_dims[3];
+  int in_start[3], out_start[3];
+  int n1, n2;              // transverse counts
+  int pass;                // 0 closed solve, >0 iterated
+  int last;                // 1 if this pass writes the output
+  int deg;                 // 1 or 2
+  unsigned long long in_box, out_box;  // scratch box sizes (elements)
+  int *status;
+};
+
+struct OpSet {           // device copies per distinct block size
+  int N;
+  LineTables tab[2];     // degree 1, 2
+};
+
+}  // namespace cfd
+
+struct cfd_scheme_s {
+  cfd::SchemeCoef s[2];
+};
+
+struct cfd_blocks_s {
+  cfd::SchemeCoef s[2];
+  int device = 0;
+  int nblocks = 0, ng = 0;
+  cfd_dtype dtype = CFD_F64;
+  std::vector<int> n;                  // per block
+  std::vector<int> nbr;                // [nblocks * 26]
+  std::vector<double> dx;              // [nblocks * 3]
+  std::vector<long long> extpre, intpre;
+  std::vector<int> sizes;              // distinct N, increasing
+  std::vector<std::vector<int>> groups;  // block ids per distinct N
+  std::vector<cfd::OpSet> ops;         // per distinct N
+  bool iter_ok = true;                 // same-size face neighbours everywhere
+  // device copies
+  int *d_nbr = nullptr;
+  long long *d_extpre = nullptr, *d_intpre = nullptr;
+  double *d_scale = nullptr;
+  int *d_nvec = nullptr;
+  std::vector<int *> d_groups;
+  int *d_status = nullptr;
+  // dense operators for the tensor-core path (per distinct N), see dense_tc.cu
+  std::vector<void *> d_dense;
+};
+
+namespace cfd {
+
+void set_error(const std::string &msg);
+cfd_status cuda_fail(cudaError_t e, const char *what);
+
+// launch accounting (profile.cpp)
+enum KernelFamily { KF_EXCHANGE = 0, KF_LINE = 1, KF_RK = 2, KF_DENSE = 3, KF_HALO = 4, KF_COUNT = 5 };
+void launch_begin(int family, cudaStream_t st);
+void launch_end(int family, cudaStream_t st);
+
+// kernels (banded.cu)
+cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nfields, cudaStream_t st);
+cfd_status launch_line(const LineParams &P, const LineTables &T, cudaStream_t st, cfd_dtype dt);
+
+}  // namespace cfd
