@@ -34,6 +34,8 @@ CFD_F64, CFD_F32 = 0, 1
 # ops
 OPS = ("dx", "dy", "dz", "dxx", "dyy", "dzz", "dxy", "dxz", "dyz")
 OP_BITS = {name: 1 << i for i, name in enumerate(OPS)}
+CFD_OP_DX, CFD_OP_DY, CFD_OP_DZ, CFD_OP_DXX, CFD_OP_DYY, CFD_OP_DZZ, CFD_OP_DXY, CFD_OP_DXZ, CFD_OP_DYZ = \
+    (1 << i for i in range(9))
 CFD_OP_ALL = 0x1FF
 
 EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd_blocks_bind",

@@ -54,3 +54,12 @@ def oracle_out_to_blocks(res_op, N):
     """(nbz, nby, nbx, N,N,N) -> (nblocks, N,N,N)."""
     nbz, nby, nbx = res_op.shape[:3]
     return res_op.reshape(nbz * nby * nbx, N, N, N)
+
+
+def wavenumber(name, eta):
+    """eta~^d of a centred scheme (Eq. fdpwerrdef written out for alpha^(d) = (a, 1, a))."""
+    e = SCHEMES[name]
+    M = (len(e["rhs"]) - 1) // 2
+    num = sum(e["rhs"][i] * np.exp(1j * (i - M) * eta) for i in range(2 * M + 1))
+    den = 1 + 2 * e["a"] * np.cos(eta)
+    return (num / den / (1j ** e["d"])).real
