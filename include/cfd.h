@@ -172,6 +172,39 @@ cfd_status cfd_apply(cfd_blocks_t blocks, const void *fields, int nfields, unsig
                      cfd_precision prec, int n_iter, void *out, void *work, size_t work_bytes,
                      void *stream);
 
+/*
+ * Allocation-free variant of cfd_apply for callers that cannot allocate
+ * device memory when they call it (no counterpart in the paper).  Such
+ * callers are typically host codes that give all device memory to their own
+ * pool at start-up and forbid later cudaMalloc/cudaFree, solver loops under a
+ * fixed memory budget, or loops that must not synchronise the device the way
+ * cudaFree does.  They bind the blocks once at start-up (cfd_blocks_bind
+ * allocates) and then call this instead of cfd_apply.
+ *
+ * It computes exactly what cfd_apply(blocks, fields, nfields, op_mask,
+ * CFD_FP64_BANDED, 0, out, ...) computes -- closures only, no hybrid
+ * iteration -- but takes no workspace: its scratch (the inner D_j of the mixed
+ * derivatives, Sec. "Z4c: system description") is one file-scope device
+ * array of 64 MiB that every GPU loading the library holds until the process
+ * exits.  A request whose scratch would exceed 64 MiB (nfields x, per block,
+ * (N+2ng) N^2 doubles when op_mask has a mixed op) fails with CFD_ERR_ARG and
+ * a message; split the fields or blocks over several calls.  Single-axis ops
+ * need no scratch.
+ *
+ * The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture.  On success the call allocates nothing,
+ * host or device, and calls no allocating routine (with the profiling
+ * diagnostics off, their default).  All calls share the one array, which keeps
+ * the previous call's contents; nothing in it needs to start at zero.  Calls
+ * whose device work overlaps in time (other streams, other host threads on
+ * the same device) race on the array: order them on one stream or serialise
+ * them.  Errors: as cfd_apply, plus CFD_ERR_ARG when the current device is
+ * not the device the blocks were bound on.
+ */
+cfd_status cfd_apply_static(cfd_blocks_t blocks, const void *fields, int nfields, unsigned op_mask, void *out,
+                            void *stream);
+
 /* Device workspace of cfd_wave_rk_step (bytes). */
 cfd_status cfd_wave_workspace(cfd_blocks_t blocks, cfd_precision prec, int n_iter, size_t *bytes);
 

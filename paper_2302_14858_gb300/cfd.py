@@ -41,7 +41,7 @@ CFD_OP_ALL = 0x1FF
 EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd_blocks_bind",
            "cfd_blocks_destroy", "cfd_exchange_ghosts", "cfd_apply_workspace", "cfd_apply",
            "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_sync_status", "cfd_last_error",
-           "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read")
+           "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static")
 KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4}
 
 
@@ -73,6 +73,8 @@ _lib.cfd_apply_workspace.argtypes = [c_void_p, c_int, c_uint, c_int, c_int, POIN
 _lib.cfd_apply_workspace.restype = c_int
 _lib.cfd_apply.argtypes = [c_void_p, c_void_p, c_int, c_uint, c_int, c_int, c_void_p, c_void_p, c_size_t, c_void_p]
 _lib.cfd_apply.restype = c_int
+_lib.cfd_apply_static.argtypes = [c_void_p, c_void_p, c_int, c_uint, c_void_p, c_void_p]
+_lib.cfd_apply_static.restype = c_int
 _lib.cfd_wave_workspace.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
 _lib.cfd_wave_workspace.restype = c_int
 _lib.cfd_wave_rk_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_size_t, c_void_p]
@@ -202,6 +204,15 @@ def cfd_apply(blocks: Blocks, fields, nfields: int, op_mask: int, prec: int, n_i
     nbytes = 0 if work is None else (work.numel() * work.element_size() if hasattr(work, "numel") else 1 << 62)
     _check(_lib.cfd_apply(blocks.handle, _ptr(fields), nfields, op_mask, prec, n_iter, _ptr(out), _ptr(work),
                           nbytes, _stream(stream)))
+
+
+def cfd_apply_static(blocks: Blocks, fields, nfields: int, op_mask: int, out, stream=None):
+    """cfd_apply (FP64 banded, closures only) with its scratch in the library's static device array.
+
+    For callers that cannot allocate device memory at the call site; see
+    include/cfd.h for the 64 MiB limit and the first-call set-up.
+    """
+    _check(_lib.cfd_apply_static(blocks.handle, _ptr(fields), nfields, op_mask, _ptr(out), _stream(stream)))
 
 
 def cfd_wave_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:

@@ -639,3 +639,23 @@ cfd_status cfd_sync_status(cfd_blocks_t B, void *stream) {
 }
 
 }  // extern "C"
+
+// Internal hooks for the allocation-free entry point (static_scratch.cu):
+// the FP64 banded apply with closures only, running on a caller-provided
+// scratch region instead of the workspace argument.
+namespace cfd {
+
+size_t banded_closed_scratch_bytes(const cfd_blocks_s *B, int nf, unsigned mask) {
+  size_t sc = 0, ha = 0;
+  banded_workspace_sizes(B, nf, mask, 0, &sc, &ha);
+  return sc * sizeof(double);
+}
+
+cfd_status apply_banded_closed(cfd_blocks_s *B, const void *fields, int nf, unsigned mask, void *out,
+                               double *scratch, cudaStream_t st) {
+  Workspace ws;
+  ws.scratch = scratch;
+  return apply_banded(B, fields, nf, mask, 0, out, ws, st);
+}
+
+}  // namespace cfd
