@@ -39,14 +39,16 @@ PREC = {"fp64_banded": 0, "tc_bf16x3": 1, "tc_bf16_exact": 2, "tc_tf32": 3}
 DTYPE_NAME = {0: "f64", 1: "f64", 2: "f64", 3: "f64"}
 
 WORKLOADS = {
-    # 128^3 periodic, 512 blocks of 16^3, 4 FP64 fields, 9 ops, one hybrid iteration
-    "cfd128_b16_f4_fp64": dict(kind="uniform", NM=128, N=16, nf=4, fields=2, dtype="f64", n_iter=1),
-    # 256^3 periodic, 512 blocks of 32^3, 4 FP64 fields, 9 ops, one hybrid iteration
-    "cfd256_b32_f4_fp64": dict(kind="uniform", NM=256, N=32, nf=4, fields=3, dtype="f64", n_iter=1),
+    # 256^3 periodic, 512 blocks of 32^3, 4 FP64 fields, 9 ops, closed blocks (dense D = A^-1 B)
+    "cfd256_b32_f4_fp64": dict(kind="uniform", NM=256, N=32, nf=4, fields=3, dtype="f64", n_iter=0),
+    # 128^3 periodic, 512 blocks of 16^3, 4 FP64 fields, 9 ops
+    "cfd128_b16_f4_fp64": dict(kind="uniform", NM=128, N=16, nf=4, fields=2, dtype="f64", n_iter=0),
+    # 128^3 periodic, 64 blocks of 32^3, 4 FP64 fields: the small case for ncu captures
+    "cfd128_b32_f4_fp64": dict(kind="uniform", NM=128, N=32, nf=4, fields=3, dtype="f64", n_iter=0),
     # 448 blocks 16^3 + 64 blocks 32^3, 22 FP32 fields, 9 ops, closures only
     "box448x16_64x32_f22_fp32": dict(kind="boxinbox", nf=22, fields=4, dtype="f32", n_iter=0),
 }
-DEFAULT_WORKLOAD = "cfd128_b16_f4_fp64"
+DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 
 
 def scheme_descs():
@@ -124,24 +126,31 @@ class ClockSampler:
 def build_workload(name, dev, torch):
     from paper_2302_14858_gb300 import workloads as W
     spec = WORKLOADS[name]
-    if spec["kind"] == "uniform":
-        mesh = W.uniform_mesh(spec["NM"], spec["N"], 4)
-    else:
-        mesh = W.box_in_box_mesh(4)
-    cfgid = spec["fields"]
-    funcs = W.workload_fields(cfgid)[: spec["nf"]]
+    funcs = W.workload_fields(spec["fields"])[: spec["nf"]]
     tdt = torch.float64 if spec["dtype"] == "f64" else torch.float32
-    # evaluate the analytic fields on the device, block by block (same formulas as workloads.sample)
+    if spec["kind"] == "uniform":
+        NM, N, g = spec["NM"], spec["N"], 4
+        mesh = W.uniform_mesh(NM, N, g)
+        nb, E = NM // N, N + 2 * g
+        x = (torch.arange(NM, dtype=torch.float64, device=dev) + 0.5) * (2 * math.pi / NM)
+        Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+        idx = (torch.arange(nb, device=dev)[:, None] * N + torch.arange(-g, N + g, device=dev)[None, :]) % NM
+        fields = torch.empty((mesh.nblocks, len(funcs), E, E, E), dtype=tdt, device=dev)
+        for q, f in enumerate(funcs):
+            fg = _eval_torch(f, X, Y, Z, torch)
+            ext = fg[idx[:, None, None, :, None, None], idx[None, :, None, None, :, None],
+                     idx[None, None, :, None, None, :]]
+            fields[:, q] = ext.reshape(mesh.nblocks, E, E, E).to(tdt)
+            del fg, ext
+        del X, Y, Z
+        return spec, mesh, fields.reshape(-1)
+    mesh = W.box_in_box_mesh(4)
     parts = []
     for b in range(mesh.nblocks):
         xs = [torch.as_tensor(c, device=dev, dtype=torch.float64) for c in mesh.coords(b)]
         Z, Y, X = torch.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
-        vals = []
-        for f in funcs:
-            vals.append(_eval_torch(f, X, Y, Z, torch).to(tdt))
-        parts.append(torch.stack(vals).reshape(-1))
-    fields = torch.cat(parts)
-    return spec, mesh, fields
+        parts.append(torch.stack([_eval_torch(f, X, Y, Z, torch).to(tdt) for f in funcs]).reshape(-1))
+    return spec, mesh, torch.cat(parts)
 
 
 def _eval_torch(f, X, Y, Z, torch):
@@ -265,15 +274,66 @@ def cpu_baseline(spec, seconds=12.0):
 # ------------------------------------------------------------------ main
 
 
+def algorithmic_bytes(nint, nf, nops, elem):
+    """Minimal HBM traffic of one apply: read every field value once, write every output once."""
+    return nint * nf * elem * (1 + nops)
+
+
+def tc_flops(mesh, nf, slices_pairs, g=4):
+    """Tensor-core flops of the dense path per apply (9 ops, closures only, one mixed order)."""
+    total = 0
+    for b in range(mesh.nblocks):
+        N = int(mesh.n[b])
+        E = N + 2 * g
+        Kp = (E + 15) // 16 * 16
+        pen = N * N
+        total += 3 * pen * 2 * N * Kp * 2 * slices_pairs            # d_a and d_aa tiles
+        total += 3 * (E * N * N * Kp * 2 + pen * N * Kp * 2) * slices_pairs  # mixed: two stages
+    return total * nf
+
+
+def max_abs_diff_per_field_op(out, ref, mesh, nf, nops, torch):
+    """max |out - ref| and max |ref| per (field, op) over all blocks (outputs [block][field][op][N^3])."""
+    errs = torch.zeros(nf, nops, dtype=torch.float64, device=out.device)
+    maxs = torch.zeros_like(errs)
+    off, b = 0, 0
+    while b < mesh.nblocks:
+        e = b
+        while e < mesh.nblocks and mesh.n[e] == mesh.n[b]:
+            e += 1
+        n3 = int(mesh.n[b]) ** 3
+        cnt = (e - b) * nf * nops * n3
+        o = out[off:off + cnt].view(e - b, nf, nops, n3)
+        r = ref[off:off + cnt].view(e - b, nf, nops, n3)
+        for q in range(nf):   # per field keeps the temporaries small
+            errs[q] = torch.maximum(errs[q], (o[:, q].double() - r[:, q].double()).abs().amax(dim=(0, 2)))
+            maxs[q] = torch.maximum(maxs[q], r[:, q].double().abs().amax(dim=(0, 2)))
+        off += cnt
+        b = e
+    return errs, maxs
+
+
+def timed(step, steps, stream, torch):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp64_banded", choices=sorted(PREC))
+    ap.add_argument("--prec", default="tc_bf16_exact", choices=sorted(PREC))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-iter", type=int, default=None)
+    ap.add_argument("--compare-steps", type=int, default=5, help="timed steps of the FP64 banded comparison")
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -308,8 +368,10 @@ def main():
     prec = PREC[args.prec]
     n_iter = spec["n_iter"]
     nint = int(sum(int(n) ** 3 for n in mesh.n))
-    out = torch.empty(nint * nf * nops, dtype=fields.dtype, device=dev)
-    ws = cfd.cfd_apply_workspace(blocks, nf, mask, prec, n_iter)
+    units = nint * nf * nops
+    out = torch.empty(units, dtype=fields.dtype, device=dev)
+    ws = max(cfd.cfd_apply_workspace(blocks, nf, mask, prec, n_iter),
+             cfd.cfd_apply_workspace(blocks, nf, mask, cfd.CFD_FP64_BANDED, n_iter))
     work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -334,42 +396,75 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms_step = timed(step, args.steps, stream, torch)
     barrier()
     clk = clocks.stop()
     cfd.cfd_sync_status(blocks, stream)
-    ms_total = ev0.elapsed_time(ev1)
     launches = cfd.cfd_kernel_launches() - launches0
     prof = {name: cfd.cfd_profile_read(fid) for name, fid in cfd.KERNEL_FAMILIES.items()}
     cfd.cfd_profile_enable(False)
-
-    ms_step = ms_total / args.steps
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    units = nint * nf * nops
     value = units * world / (ms_step * 1e-3) / 1e9
+    ms_total = ms_step * args.steps
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel family, from the per-launch event times of the timed region
     fam, (nl, tl) = max(prof.items(), key=lambda kv: kv[1][1])
+    elem = fields.element_size()
     if fam == "line":
         fl = banded_flops_per_step(mesh, nf, cfd.OPS, n_iter) * args.steps
         achieved = fl / (tl * 1e-3) / 1e9
         roof = {"kernel": "k_line (FP64 banded pencil solve)", "bound": "alu", "achieved": round(achieved, 2),
                 "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s", "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table)",
-                "launches_per_step": nl / args.steps, "avg_launch_ms": tl / max(nl, 1),
-                "share_of_step": round(tl / ms_total, 4), "traffic": None}
-    else:
-        roof = {"kernel": fam, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table; 1.256 measured)",
                 "traffic": None}
+    else:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                peaks = json.load(fh)
+        except OSError:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        byts = algorithmic_bytes(nint, nf, nops, elem) * args.steps
+        achieved = byts / (tl * 1e-3) / 1e9
+        pairs = 15 if prec == PREC["tc_bf16_exact"] else 3
+        tcf = tc_flops(mesh, nf, pairs) * args.steps / (tl * 1e-3) / 1e12
+        roof = {"kernel": "k_dense (tcgen05 BF16 digit-slice GEMM)", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_point_op": round(elem * (1 + nops) / nops, 3),
+                "tensor_tflops": round(tcf, 1),
+                "tensor_frac_of_bf16_peak": round(tcf / float(peaks.get("bf16_tflops", 1900.0)), 4),
+                "traffic": None}
+    roof.update({"launches_per_step": nl / args.steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
+                 "share_of_step": round(tl / ms_total, 4)})
+
+    # the FP64 banded solve on the same inputs: speed and max relative difference per (field, op)
+    compare = None
+    if not args.no_compare and prec != PREC["fp64_banded"]:
+        ref = torch.empty_like(out)
+
+        def step64():
+            cfd.cfd_exchange_ghosts(blocks, fields, nf, stream)
+            cfd.cfd_apply(blocks, fields, nf, mask, cfd.CFD_FP64_BANDED, n_iter, ref, work, stream)
+
+        step64()
+        torch.cuda.synchronize()
+        ms64 = timed(step64, args.compare_steps, stream, torch)
+        step()
+        torch.cuda.synchronize()
+        errs, maxs = max_abs_diff_per_field_op(out, ref, mesh, nf, nops, torch)
+        rel = (errs / maxs).cpu().numpy()
+        worst = float(rel.max())
+        compare = {"fp64_banded": {"value": round(units / (ms64 * 1e-3) / 1e9, 4), "ms_per_step": round(ms64, 4)},
+                   "speedup_vs_fp64_banded": round(ms64 / ms_step, 3),
+                   "max_rel_err_vs_fp64_banded": worst,
+                   "max_rel_err_per_op": {op: float(rel[:, i].max()) for i, op in enumerate(cfd.OPS)}}
+        del ref
 
     # end-to-end through the C ABI with host buffers
     e2e = None
@@ -377,22 +472,16 @@ def main():
         host_in = torch.empty(fields.numel(), dtype=fields.dtype, pin_memory=True)
         host_in.copy_(fields)
         host_out = torch.empty(out.numel(), dtype=out.dtype, pin_memory=True)
-        for _ in range(2):
+
+        def step_e2e():
             fields.copy_(host_in, non_blocking=True)
             step()
             host_out.copy_(out, non_blocking=True)
+
+        step_e2e()
         torch.cuda.synchronize()
-        ke = max(3, args.steps // 4)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
-        e0.record(stream)
-        for _ in range(ke):
-            fields.copy_(host_in, non_blocking=True)
-            step()
-            host_out.copy_(out, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_e2e = e0.elapsed_time(e1) / ke
+        ms_e2e = timed(step_e2e, max(3, min(20, args.steps // 10)), stream, torch)
         e2e = {"value": round(units * world / (ms_e2e * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s",
                "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
                "d2h_bytes_per_step": host_out.numel() * host_out.element_size(),
@@ -413,8 +502,8 @@ def main():
                        "blocks": mesh.nblocks, "points_per_field": nint,
                        "l2": "inputs larger than L2" if in_bytes > L2_BYTES else "inputs fit L2",
                        "input_bytes": in_bytes, "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk,
+            "roofline": roof, "compare": compare, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line))
     if world > 1:

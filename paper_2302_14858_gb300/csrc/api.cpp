@@ -464,7 +464,8 @@ void cfd_blocks_destroy(cfd_blocks_t B) {
   cudaFree(B->d_nvec);
   cudaFree(B->d_status);
   for (int *p : B->d_groups) cudaFree(p);
-  for (void *p : B->d_dense) cudaFree(p);
+  for (void *p : B->d_dense_ptrs) cudaFree(p);
+  if (B->dense_state && B->dense_free) B->dense_free(B->dense_state);
   cudaSetDevice(prev);
   delete B;
 }

@@ -103,8 +103,11 @@ struct cfd_blocks_s {
   int *d_nvec = nullptr;
   std::vector<int *> d_groups;
   int *d_status = nullptr;
-  // dense operators for the tensor-core path (per distinct N), see dense_tc.cu
-  std::vector<void *> d_dense;
+  // dense operators for the tensor-core path (per distinct N), see dense_tc.cu:
+  // host-side state, its deleter, and the device allocations it refers to
+  void *dense_state = nullptr;
+  void (*dense_free)(void *) = nullptr;
+  std::vector<void *> d_dense_ptrs;
 };
 
 namespace cfd {

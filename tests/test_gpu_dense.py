@@ -1,0 +1,182 @@
+"""GPU parity of the tensor-core dense path (tcgen05, BF16 digit slices) against the oracle.
+
+Tolerances (relative max error per field and op, against the FP64 oracle):
+  exact slices (CFD_TC_BF16_EXACT)  <= 1e-7 on FP64 fields: the design bound is
+      ~2^-37 of sum_j |D_ij f_j| (discarded slice pairs and digit remainders),
+      times the cancellation sum_j |D_ij f_j| / max |D f|.  That factor grows
+      like dx^-d: ~370 for d_xx of a Gaussian at 64^3 (measured error 2.8e-9),
+      ~6000 at 256^3 (bound 4.4e-8).  The contract of the path is 1e-6;
+  exact slices on FP32 fields     <= 1e-6 (one FP32 rounding of the output dominates);
+  3-product split (CFD_TC_BF16X3)   measured bound, asserted <= 5e-2 (not an FP64-grade mode).
+"""
+import numpy as np
+import pytest
+
+from oracle import cfd as C
+from paper_2302_14858_gb300 import workloads as W
+from tests.helpers import OPS, desc, oracle_sch, rel_max
+
+pytestmark = pytest.mark.gpu
+
+TOL_EXACT64 = 1e-7
+TOL_EXACT32 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_14858_gb300 import build
+    build.build()
+    from paper_2302_14858_gb300 import cfd
+    return cfd
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def apply(lib, torch, B, buf, nf, mask, prec, n_iter=0, dtype=np.float64):
+    dev = torch.device("cuda", 0)
+    fields = torch.from_numpy(np.ascontiguousarray(buf.astype(dtype))).to(dev)
+    nops = bin(mask).count("1")
+    nint = sum(int(n) ** 3 for n in B.block_n)
+    out = torch.full((nint * nf * nops,), float("nan"), dtype=fields.dtype, device=dev)
+    ws = lib.cfd_apply_workspace(B, nf, mask, prec, n_iter)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    lib.cfd_apply(B, fields, nf, mask, prec, n_iter, out, work)
+    lib.cfd_sync_status(B)
+    return out.cpu().numpy()
+
+
+def uniform(NM, N, g, fields):
+    mesh = W.uniform_mesh(NM, N, g)
+    dx = 2 * np.pi / NM
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    exts = [C.ghost_fill_3d(f(X, Y, Z), N, g) for f in fields]
+    E = N + 2 * g
+    buf = np.stack([e.reshape(mesh.nblocks, E, E, E) for e in exts], axis=1).reshape(-1)
+    return mesh, dx, exts, buf
+
+
+def fields4(seed):
+    r = W.rng(seed)
+    return [W.sine_sum(r, 8, 1, 12), W.gaussian(r, 0.1), W.sine_sum(r, 8, 1, 12), W.gaussian(r, 0.1)]
+
+
+@pytest.mark.parametrize("NM,N", [(64, 16), (64, 32), (128, 32)])
+def test_exact_slices_all_ops(lib, torch, NM, N):
+    g = 4
+    fs = fields4(300 + NM + N)
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    nf = len(fs)
+    got = apply(lib, torch, B, buf, nf, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT).reshape(mesh.nblocks, nf, 9, N, N, N)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = {}
+    for q in range(nf):
+        ref = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, 0)
+        for i, op in enumerate(OPS):
+            worst[(q, op)] = rel_max(got[:, q, i], ref[op].reshape(mesh.nblocks, N, N, N))
+    print("exact-slice max rel err", max(worst.values()))
+    for k, v in worst.items():
+        assert v < TOL_EXACT64, (k, v)
+
+
+def test_exact_slices_match_banded_fp64_full_size(lib, torch):
+    """128^3 as 512 blocks of 16^3, 4 fields, 9 ops: tensor-core vs the GPU FP64 banded solve."""
+    NM, N, g = 128, 16, 4
+    fs = fields4(2302 + 2)
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    tc = apply(lib, torch, B, buf, 4, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT).reshape(mesh.nblocks, 4, 9, -1)
+    fp = apply(lib, torch, B, buf, 4, lib.CFD_OP_ALL, lib.CFD_FP64_BANDED).reshape(mesh.nblocks, 4, 9, -1)
+    errs = [rel_max(tc[:, q, i], fp[:, q, i]) for q in range(4) for i in range(9)]
+    print("tc vs fp64 banded max rel err", max(errs))
+    assert max(errs) < TOL_EXACT64
+
+
+def test_bf16x3_measured_bound(lib, torch):
+    NM, N, g = 64, 16, 4
+    fs = fields4(77)
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    got = apply(lib, torch, B, buf, 4, lib.CFD_OP_ALL, lib.CFD_TC_BF16X3).reshape(mesh.nblocks, 4, 9, N, N, N)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = 0.0
+    for q in range(4):
+        ref = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, 0)
+        for i, op in enumerate(OPS):
+            worst = max(worst, rel_max(got[:, q, i], ref[op].reshape(mesh.nblocks, N, N, N)))
+    print("bf16x3 max rel err", worst)
+    assert worst < 5e-2
+
+
+def test_exact_slices_single_periodic_block(lib, torch):
+    NM = N = 32
+    g = 4
+    f = W.workload_fields(1)[0]
+    mesh, dx, exts, buf = uniform(NM, N, g, [f])
+    s = lib.cfd_scheme_create(desc("P2_d1"), desc("P2_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    got = apply(lib, torch, B, buf, 1, lib.op_mask(["dx", "dyy"]), lib.CFD_TC_BF16_EXACT).reshape(2, N, N, N)
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    fg = f(X, Y, Z)
+    want_dx = C.global_periodic(np.moveaxis(fg, 2, 0), oracle_sch("P2_d1"), dx)
+    want_dyy = C.global_periodic(np.moveaxis(fg, 1, 0), oracle_sch("P2_d2"), dx)
+    assert rel_max(got[0], np.moveaxis(want_dx, 0, 2)) < TOL_EXACT64
+    assert rel_max(got[1], np.moveaxis(want_dyy, 0, 1)) < TOL_EXACT64
+
+
+def test_exact_slices_fp32_uneven_blocks(lib, torch):
+    """Blocks of 16^3 and 32^3 with analytic ghosts on the level interface, FP32 fields."""
+    # 16^3 coarse blocks with a 2:1 refined octant of 32^3 blocks (both sizes run on the tensor cores)
+    nc = 4
+    ns, origins, ds, ci, fi = [], [], [], {}, {}
+    for bz in range(nc):
+        for by in range(nc):
+            for bx in range(nc):
+                if bx < 2 and by < 2 and bz < 2:
+                    continue
+                ci[(bz, by, bx)] = len(ns)
+                ns.append(16)
+                origins.append((bx * 16, by * 16, bz * 16))
+                ds.append(2 * np.pi / 64)
+    for bz in range(2):
+        for by in range(2):
+            for bx in range(2):
+                fi[(bz, by, bx)] = len(ns)
+                ns.append(32)
+                origins.append((bx * 32, by * 32, bz * 32))
+                ds.append(np.pi / 64)
+    nbr = np.full((len(ns), 26), -1, np.int32)
+    for (bz, by, bx), b in ci.items():
+        for r, (dz, dy, dxx) in enumerate(W.DIRS):
+            nbr[b, r] = ci.get(((bz + dz) % nc, (by + dy) % nc, (bx + dxx) % nc), -1)
+    for (bz, by, bx), b in fi.items():
+        for r, (dz, dy, dxx) in enumerate(W.DIRS):
+            nbr[b, r] = fi.get((bz + dz, by + dy, bx + dxx), -1)
+    mesh = W.Mesh(np.asarray(ns), np.asarray(origins), np.repeat(np.asarray(ds)[:, None], 3, 1), nbr, 4)
+    fields = W.workload_fields(4)[:2]
+    per_block = W.sample(mesh, fields, dtype=np.float32)
+    buf = W.pack(per_block)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, 4, lib.CFD_F32)
+    out = apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, dtype=np.float32)
+    got = W.unpack(out, mesh, 2, interior=True, nops=9)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = 0.0
+    for q in range(2):
+        for i, op in enumerate(OPS):
+            want = [C.apply_block(per_block[b][q].astype(np.float64), s1, s2, mesh.dx[b], int(mesh.n[b]), 4, (op,))[op]
+                    for b in range(mesh.nblocks)]
+            wmax = max(np.abs(w).max() for w in want)
+            err = max(np.abs(got[b][q, i].astype(np.float64) - want[b]).max() for b in range(mesh.nblocks)) / wmax
+            worst = max(worst, err)
+    print("fp32 exact-slice max rel err", worst)
+    assert worst < TOL_EXACT32
