@@ -488,6 +488,7 @@ cfd_status cfd_blocks_bind(cfd_scheme_t scheme, int nblocks, const int *block_n,
   B->s[0] = scheme->s[0];
   B->s[1] = scheme->s[1];
   cudaGetDevice(&B->device);
+  if (cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess) B->num_sms = 0;
   B->nblocks = nblocks;
   B->ng = ng;
   B->dtype = dtype;

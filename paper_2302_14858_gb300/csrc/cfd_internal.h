@@ -85,7 +85,7 @@ struct cfd_scheme_s {
 
 struct cfd_blocks_s {
   cfd::SchemeCoef s[2];
-  int device = 0;
+  int device = 0, num_sms = 0;
   int nblocks = 0, ng = 0;
   cfd_dtype dtype = CFD_F64;
   std::vector<int> n;                  // per block

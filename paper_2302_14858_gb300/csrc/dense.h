@@ -8,23 +8,25 @@ namespace cfd {
 // 128-pencil tiles against the digit images of up to two operators per pass.
 struct DenseParams {
   const void *in;            // field buffer (dtype) or FP64 scratch
-  void *out;                 // final output buffer (dtype)
-  void *scratch_out;         // FP64 scratch for intermediate results
+  void *out;                 // final output buffer (dtype): block b, field q, op -> N^3 box
+  double *scratch_out;       // FP64 scratch box of this stage (or null)
   const int *blocks;         // [nblk] global block ids
   const long long *extpre, *intpre;
   int nblk, nf, nops, N, g;
   int in_field;              // 1: in is the field buffer
-  unsigned long long in_box, out_box;  // scratch box sizes (elements)
+  unsigned long long in_box, sc_box;  // scratch box sizes (elements per block and field)
   int axis, t1, t2;          // box axes (0 z, 1 y, 2 x); t2 fastest
-  int in_dims[3], out_dims[3], in_start[3], out_start[3];
+  int in_dims[3], in_start[3];        // input box and the start of the pencil range
+  int sc_dims[3], sc_start[3];        // scratch output box and offset of pencil (t1, t2)
   int n1, n2;                // transverse pencil counts
-  int int_lo1, int_hi1, int_lo2, int_hi2;  // transverse range that writes final outputs
-  int passes, rows;          // MMA passes per tile, output rows per pass (multiple of 16, <= 48)
+  int int_lo1, int_hi1, int_lo2, int_hi2;  // pencils that write final outputs (interior)
+  int passes, rows;          // MMA passes per tile, output rows per pass (16 or 32)
   int nseg[2];               // operators (segments of N rows) per pass
   const uint16_t *seg_img[2][2];
   const int *seg_exp[2][2];
-  int seg_mode[2][2];        // -1 skip, 0 final store, 2 FP64 scratch
+  int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both
   int seg_op[2][2];          // op index in the output for final stores
+  int tiles_per_job, ntiles; // 128-pencil tiles per (block, field); all tiles of the stage
   int *status;
 };
 

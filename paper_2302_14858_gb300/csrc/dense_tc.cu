@@ -48,7 +48,7 @@ namespace {
 
 constexpr int kS = 5;              // digit slices kept for exact mode
 constexpr int kTile = 128;         // pencils per tile (MMA M)
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (~2 s) before giving up
 
 // ------------------------------------------------------------------ host: operator digits
@@ -178,40 +178,26 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ uint32_t small_int_bf16(int a) {
-  // exact for |a| < 2^22: 1.5 * 2^23 + a, then drop the low 16 (zero) mantissa bits
-  const float f = __int_as_float(0x4B400000 + a) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
+// BF16 bit pattern (high half of a float) of a small integer, exact for |a| < 2^22.
+__device__ __forceinline__ uint32_t small_int_f32bits(int a) {
+  return __float_as_uint(__int_as_float(0x4B400000 + a) - 12582912.0f);
 }
 
+// Integer value of an FP32 accumulator holding an exact integer below 2^22.
 __device__ __forceinline__ int acc_to_int(uint32_t bits) {
   return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
 }
 
-// Y * 2^E as an IEEE double, rounded to nearest even, from integer arithmetic.
+// Y * 2^E as an IEEE double, truncated to 53 bits (error below one unit in
+// the last place), built with integer instructions only.
 __device__ __forceinline__ double scaled_int_to_double(long long Y, int E) {
-  if (Y == 0) return 0.0;
-  const unsigned long long sgn = Y < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long sgn = (unsigned long long)Y & (1ull << 63);
   unsigned long long U = Y < 0 ? (unsigned long long)(-Y) : (unsigned long long)Y;
-  const int msb = 63 - __clzll((long long)U);
-  int ex = msb + E;
-  unsigned long long mant;
-  if (msb > 52) {
-    const int sh = msb - 52;
-    unsigned long long q = U >> sh;
-    const unsigned long long rem = U & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (q & 1ull))) {
-      ++q;
-      if (q >> 53) { q >>= 1; ++ex; }
-    }
-    mant = q;
-  } else {
-    mant = U << (52 - msb);
-  }
-  const int be = ex + 1023;
-  if (be <= 0) return __longlong_as_double((long long)sgn);
-  if (be >= 2047) return __longlong_as_double((long long)(sgn | (0x7FFull << 52)));
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
+  const int lz = __clzll((long long)U);
+  U <<= (lz & 63);
+  const int be = 63 - lz + E + 1023;
+  const unsigned long long bits = sgn | ((unsigned long long)be << 52) | ((U >> 11) & ((1ull << 52) - 1));
+  return (U == 0 || be <= 0) ? __longlong_as_double((long long)sgn) : __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ float scaled_int_to_float(long long Y, int E) {
@@ -221,27 +207,44 @@ __device__ __forceinline__ float scaled_int_to_float(long long Y, int E) {
   return y * __int_as_float((E + 127) << 23);
 }
 
-// Fixed-point value F = round(v / tau * 2^39) of one input element.
+// Signed fixed-point value F = round(v / tau * 2^39), |F| <= 2^39, of one input
+// element; tau = 2^(emax - bias + 1) is the pencil's power-of-two scale.
 __device__ __forceinline__ long long fixed_of(double v, int emax) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((u >> 52) & 0x7FF);
-  if (e == 0) return 0;
   const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);
   const int sh = emax + 14 - e;  // >= 14
-  long long F = sh < 63 ? (long long)((m + (1ull << (sh - 1))) >> sh) : 0;
-  return (u >> 63) ? -F : F;
+  const long long U = (e == 0 || sh > 60) ? 0ll : (long long)(((m >> (sh - 1)) + 1ull) >> 1);
+  return (u >> 63) ? -U : U;
 }
 
 __device__ __forceinline__ long long fixed_of(float v, int emax) {
   const uint32_t u = __float_as_uint(v);
   const int e = (int)((u >> 23) & 0xFF);
-  if (e == 0) return 0;
   const unsigned long long m = (u & 0x7FFFFFu) | 0x800000u;
   const int sh = e - emax + 15;  // <= 15
-  long long F;
-  if (sh >= 0) F = (long long)(m << sh);
-  else F = (-sh) < 40 ? (long long)((m + (1ull << (-sh - 1))) >> (-sh)) : 0;
-  return (u >> 31) ? -F : F;
+  long long U;
+  if (e == 0) U = 0;
+  else if (sh >= 0) U = (long long)(m << sh);
+  else U = (-sh) > 40 ? 0ll : (long long)(((m >> (-sh - 1)) + 1ull) >> 1);
+  return (u >> 31) ? -U : U;
+}
+
+// Balanced base-256 digits d_0..d_4 (|d| <= 128, d_0 most significant) of a
+// two's-complement F with |F| <= 2^39; returns the leading S as FP32 bit patterns.
+template <int S>
+__device__ __forceinline__ void digits_of(long long F, uint32_t (&out)[S]) {
+  const uint32_t lo = (uint32_t)F;
+  const int hi = (int)(F >> 32);
+  int d[5];
+  int c, x;
+  x = (int)(lo & 0xFF);         c = x >= 128; d[4] = x - (c << 8);
+  x = (int)((lo >> 8) & 0xFF) + c;  c = x >= 128; d[3] = x - (c << 8);
+  x = (int)((lo >> 16) & 0xFF) + c; c = x >= 128; d[2] = x - (c << 8);
+  x = (int)(lo >> 24) + c;          c = x >= 128; d[1] = x - (c << 8);
+  d[0] = hi + c;
+#pragma unroll
+  for (int t = 0; t < S; ++t) out[t] = small_int_f32bits(d[t]);
 }
 
 __device__ __forceinline__ int biased_exp(double v) {
@@ -251,31 +254,103 @@ __device__ __forceinline__ int biased_exp(float v) { return (int)((__float_as_ui
 __device__ __forceinline__ int tau_exp(int emax, double) { return emax - 1022; }
 __device__ __forceinline__ int tau_exp(int emax, float) { return emax - 126; }
 
-template <typename T>
-__device__ __forceinline__ T ldin(const T *p) { return __ldg(p); }
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t parity) {
+  const long long t0 = clock64();
+  uint32_t done = 0;
+  while (!done) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar_addr), "r"(parity));
+    if (!done && clock64() - t0 > kWaitLimit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ long long stride_of(int axis, long long s0, long long s1) {
+  return axis == 0 ? s0 : (axis == 1 ? s1 : 1ll);
+}
 
 // ------------------------------------------------------------------ the kernel
+//
+// Persistent, one CTA of 16 warps per SM.  Per 128-pencil tile:
+//   all threads:  pencil values (already in shared memory) -> 5 digit rows of A
+//   all threads:  cp.async prefetch of the next tile's pencils
+//   thread 0:     tcgen05.mma for every pass, one mbarrier commit per pass
+//   all warps:    epilogue of each pass as soon as its commit arrives
+// Warp w reads TMEM lane quadrant w % 4 (pencils 32 (w % 4) .. +31), and
+// quarter w / 4 of the K chunks (splitting) or of the pass rows (epilogue).
+
+constexpr int kThreads = 512;
+
+template <int RQ, int LEV, typename TO>
+__device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int etau, const int *rowexp,
+                                              TO *fin_base, long long fin_stride, double *sc_base,
+                                              long long sc_stride, bool write_fin, bool write_sc, int i0) {
+  uint32_t acc[LEV][RQ];
+#pragma unroll
+  for (int k = 0; k < LEV; ++k) {
+    const uint32_t addr = taddr + (uint32_t)k * lev_stride;
+    if constexpr (RQ == 8) {
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3]), "=r"(acc[k][4]),
+                     "=r"(acc[k][5]), "=r"(acc[k][6]), "=r"(acc[k][7])
+                   : "r"(addr));
+    } else {
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                   : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3])
+                   : "r"(addr));
+    }
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int c = 0; c < RQ; ++c) {
+    long long Y;
+    if constexpr (LEV == 5) {
+      const int t1 = acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]);
+      const int t2 = acc_to_int(acc[2][c]) * 256 + acc_to_int(acc[3][c]);
+      Y = ((long long)t1 << 24) + ((long long)t2 << 8) + (long long)acc_to_int(acc[4][c]);
+    } else {
+      Y = (long long)(acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]));
+    }
+    const int ex = rowexp[c] + etau - 14 - 8 * (LEV - 1);
+    const long long i = i0 + c;
+    if (write_fin) {
+      if constexpr (sizeof(TO) == 8) fin_base[i * fin_stride] = scaled_int_to_double(Y, ex);
+      else fin_base[i * fin_stride] = scaled_int_to_float(Y, ex);
+    }
+    if (write_sc) sc_base[i * sc_stride] = scaled_int_to_double(Y, ex);
+  }
+}
 
 template <typename TI, typename TO, int KP, int S, int L>
-__global__ void __launch_bounds__(128) k_dense(const DenseParams P) {
+__global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int A_BYTES = S * kTile * KP * 2;
+  constexpr int PITCH = KP + 1;  // staging row pitch (elements), odd to spread banks
+  constexpr int NCH = KP / 8;    // 8-value K chunks per pencil
+  const int R = P.rows;
+  const int B_PASS_BYTES = S * R * KP * 2;
   uint16_t *sA = reinterpret_cast<uint16_t *>(smem);
   uint16_t *sB = reinterpret_cast<uint16_t *>(smem + A_BYTES);
-  const int R = P.rows;                      // output rows per pass (<= 48)
-  const int B_PASS_BYTES = S * R * KP * 2;
-  int *s_rowexp = reinterpret_cast<int *>(smem + A_BYTES + P.passes * B_PASS_BYTES);
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + A_BYTES + P.passes * B_PASS_BYTES + 2 * 48 * 4);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  TI *stg = reinterpret_cast<TI *>(smem + A_BYTES + 2 * B_PASS_BYTES);
+  int *s_rowexp = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg) + kTile * PITCH * sizeof(TI));
+  int *s_emax = s_rowexp + 2 * 48;  // [4][128]
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(s_emax + 4 * kTile);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int np = P.n1 * P.n2;
-  const int tiles = (np + kTile - 1) / kTile;
-  const int tile = blockIdx.x % tiles;
-  const int job = blockIdx.x / tiles;
-  const int lb = job / P.nf, q = job - lb * P.nf;
-  const int b = P.blocks[lb];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, part = warp >> 2;
+  const int pl = quad * 32 + lane;  // pencil within the tile == TMEM lane
   const int N = P.N, g = P.g, E = N + 2 * g;
+  const int np = P.n1 * P.n2;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -284,205 +359,192 @@ __global__ void __launch_bounds__(128) k_dense(const DenseParams P) {
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-
-  // ---- B operand: digit images of the segments of every pass, and row exponents
+  // B operand: digit images of every pass, loaded once per CTA; row exponents
+  // of pass ps at s_rowexp[ps * 48 + row].
   for (int ps = 0; ps < P.passes; ++ps) {
     for (int sg = 0; sg < P.nseg[ps]; ++sg) {
       const uint4 *src = reinterpret_cast<const uint4 *>(P.seg_img[ps][sg]);
-      // per slice t: N rows x KP -> place at pass image, slice t, row offset sg*N
       const int slice_u4 = N * KP * 2 / 16;
       for (int t = 0; t < S; ++t) {
         uint4 *dst = reinterpret_cast<uint4 *>(sB + (size_t)ps * (B_PASS_BYTES / 2) + (size_t)t * R * KP +
                                                (size_t)sg * N * KP);
-        const uint4 *s = src + (size_t)t * slice_u4;
-        for (int i = tid; i < slice_u4; i += blockDim.x) dst[i] = __ldg(s + i);
+        const uint4 *sp = src + (size_t)t * slice_u4;
+        for (int i = tid; i < slice_u4; i += kThreads) dst[i] = __ldg(sp + i);
       }
-      for (int i = tid; i < N; i += blockDim.x) s_rowexp[ps * 48 + sg * N + i] = P.seg_exp[ps][sg][i];
+      for (int i = tid; i < N; i += kThreads) s_rowexp[ps * 48 + sg * N + i] = P.seg_exp[ps][sg][i];
     }
   }
 
-  // ---- A operand: pencil `tid` of this tile, split into S digit rows
-  const int p = tile * kTile + tid;
-  int etau = 0;
-  long long obase = 0;  // transverse part of the output offset
-  {
-    const bool valid = p < np;
-    const int t1 = valid ? p / P.n2 : 0, t2 = valid ? p - (p / P.n2) * P.n2 : 0;
-    const long long is0 = (long long)P.in_dims[1] * P.in_dims[2], is1 = P.in_dims[2];
-    const long long istr[3] = {is0, is1, 1};
-    long long ib;
-    if (P.in_field) ib = (long long)P.nf * P.extpre[b] + (long long)q * E * E * E;
-    else ib = ((long long)lb * P.nf + q) * (long long)P.in_box;
-    ib += (long long)(P.in_start[P.t1] + t1) * istr[P.t1] + (long long)(P.in_start[P.t2] + t2) * istr[P.t2];
-    const long long sa = istr[P.axis];
-    const TI *fin = static_cast<const TI *>(P.in) + ib;
-    TI v[KP];
-    int emax = 0;
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      v[j] = (valid && j < E) ? ldin(fin + (long long)j * sa) : TI(0);
-      emax = max(emax, biased_exp(v[j]));
-    }
-    etau = tau_exp(emax, TI(0));
-    const int row_group = tid >> 3, row_in = tid & 7;
-#pragma unroll
-    for (int k8 = 0; k8 < KP / 8; ++k8) {
-      uint32_t w[S][4];
-#pragma unroll
-      for (int jj = 0; jj < 8; jj += 2) {
-        long long F0 = emax ? fixed_of(v[k8 * 8 + jj], emax) : 0;
-        long long F1 = emax ? fixed_of(v[k8 * 8 + jj + 1], emax) : 0;
-        // full 5-digit split of the 39-bit fixed-point value; the leading S digits are kept
-        int d0[kS], d1[kS];
-#pragma unroll
-        for (int t = kS - 1; t >= 1; --t) {
-          int r0 = (int)(F0 & 0xFF), r1 = (int)(F1 & 0xFF);
-          r0 = r0 >= 128 ? r0 - 256 : r0;
-          r1 = r1 >= 128 ? r1 - 256 : r1;
-          d0[t] = r0;
-          d1[t] = r1;
-          F0 = (F0 - r0) >> 8;
-          F1 = (F1 - r1) >> 8;
-        }
-        d0[0] = (int)F0;
-        d1[0] = (int)F1;
-#pragma unroll
-        for (int t = 0; t < S; ++t) w[t][jj / 2] = small_int_bf16(d0[t]) | (small_int_bf16(d1[t]) << 16);
-      }
-#pragma unroll
-      for (int t = 0; t < S; ++t) {
-        uint4 *dst = reinterpret_cast<uint4 *>(sA + (size_t)t * kTile * KP +
-                                               ((size_t)row_group * (KP / 8) + k8) * 64 + row_in * 8);
-        *dst = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
-      }
-    }
-    // output offset (transverse part) of this pencil
-    const long long os0 = (long long)P.out_dims[1] * P.out_dims[2], os1 = P.out_dims[2];
-    const long long ostr[3] = {os0, os1, 1};
-    obase = (long long)(P.out_start[P.t1] + t1) * ostr[P.t1] + (long long)(P.out_start[P.t2] + t2) * ostr[P.t2];
-  }
+  const long long is0 = (long long)P.in_dims[1] * P.in_dims[2], is1 = P.in_dims[2];
+  const long long s_t1 = stride_of(P.t1, is0, is1), s_t2 = stride_of(P.t2, is0, is1), s_ax = stride_of(P.axis, is0, is1);
+  const long long f_t1 = stride_of(P.t1, (long long)N * N, N), f_t2 = stride_of(P.t2, (long long)N * N, N),
+                  f_ax = stride_of(P.axis, (long long)N * N, N);
+  const long long ss0 = (long long)P.sc_dims[1] * P.sc_dims[2], ss1 = P.sc_dims[2];
+  const long long c_t1 = stride_of(P.t1, ss0, ss1), c_t2 = stride_of(P.t2, ss0, ss1), c_ax = stride_of(P.axis, ss0, ss1);
+  const int in_s1 = P.t1 == 0 ? P.in_start[0] : (P.t1 == 1 ? P.in_start[1] : P.in_start[2]);
+  const int in_s2 = P.t2 == 0 ? P.in_start[0] : (P.t2 == 1 ? P.in_start[1] : P.in_start[2]);
+  const int sc_s1 = P.t1 == 0 ? P.sc_start[0] : (P.t1 == 1 ? P.sc_start[1] : P.sc_start[2]);
+  const int sc_s2 = P.t2 == 0 ? P.sc_start[0] : (P.t2 == 1 ? P.sc_start[1] : P.sc_start[2]);
+  const long long n3 = (long long)N * N * N;
+  const long long E3 = (long long)E * E * E;
 
-  asm volatile("fence.proxy.async.shared::cta;");
+  // issue the cp.async copies of one tile's pencils into the staging buffer
+  auto prefetch = [&](int tile) {
+    const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+    const int lb = job / P.nf, q = job - lb * P.nf;
+    const int b = P.blocks[lb];
+    const int pp = tid & (kTile - 1), jq = tid >> 7;  // pencil, first j of this thread
+    const int p = tj * kTile + pp;
+    if (p < np) {
+      const int t1 = p / P.n2, t2 = p - (p / P.n2) * P.n2;
+      long long ib = P.in_field ? (long long)P.nf * P.extpre[b] + (long long)q * E3
+                                : ((long long)lb * P.nf + q) * (long long)P.in_box;
+      ib += (long long)(in_s1 + t1) * s_t1 + (long long)(in_s2 + t2) * s_t2;
+      const TI *src = static_cast<const TI *>(P.in) + ib;
+      for (int j = jq; j < E; j += 4) {
+        if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * PITCH + j, src + (long long)j * s_ax);
+        else cp_async4(stg + pp * PITCH + j, src + (long long)j * s_ax);
+      }
+    }
+    asm volatile("cp.async.commit_group;");
+  };
+
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
   const uint32_t lbo = 128, sbo = KP * 16;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(R >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+  uint32_t phase0 = 0, phase1 = 0;
   bool failed = false;
 
-  const int pp = p < np ? p : 0;
-  const bool valid = p < np;
-  const int t1 = pp / P.n2, t2 = pp - t1 * P.n2;
-  const bool interior = (P.int_lo1 <= t1 && t1 < P.int_hi1 && P.int_lo2 <= t2 && t2 < P.int_hi2);
+  int tile = blockIdx.x;
+  if (tile < P.ntiles) prefetch(tile);
+  while (tile < P.ntiles && !failed) {
+    const int next = tile + gridDim.x;
+    const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+    const int lb = job / P.nf, q = job - lb * P.nf;
+    const int b = P.blocks[lb];
+    const int p = tj * kTile + pl;
+    const bool valid = p < np;
+    const int t1 = valid ? p / P.n2 : 0, t2 = valid ? p - (p / P.n2) * P.n2 : 0;
 
-  for (int ps = 0; ps < P.passes; ++ps) {
-    if (tid == 0) {
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB) + ps * B_PASS_BYTES;
-      bool first[L + 1];
+    asm volatile("cp.async.wait_all;");
+    __syncthreads();
+    // ---- split: this thread owns chunks c = part and part + 4 of pencil pl
+    TI v[2][8];
+    int em = 0;
 #pragma unroll
-      for (int k = 0; k <= L; ++k) first[k] = true;
+    for (int h = 0; h < 2; ++h) {
+      const int c = part + 4 * h;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-#pragma unroll
-        for (int t = 0; t < S; ++t) {
-          if (s + t > L) continue;
-          const uint32_t dcol = tmem + (uint32_t)((s + t) * R);
-#pragma unroll
-          for (int kk = 0; kk < KP / 16; ++kk) {
-            const uint64_t da = smem_desc(a0 + (uint32_t)(s * kTile * KP * 2 + kk * 256), lbo, sbo);
-            const uint64_t db = smem_desc(b0 + (uint32_t)(t * R * KP * 2 + kk * 256), lbo, sbo);
-            mma_bf16(dcol, da, db, idesc, first[s + t] ? 0u : 1u);
-            first[s + t] = false;
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(mbar)));
-    }
-    // bounded wait for this pass's phase
-    {
-      const long long t0 = clock64();
-      uint32_t done = 0;
-      while (!done) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"((uint32_t)(ps & 1)));
-        if (!done && clock64() - t0 > kWaitLimit) {
-          failed = true;
-          break;
-        }
+      for (int k = 0; k < 8; ++k) {
+        const int j = c * 8 + k;
+        v[h][k] = (c < NCH && j < E && valid) ? stg[pl * PITCH + j] : TI(0);
+        em = max(em, biased_exp(v[h][k]));
       }
     }
-    failed = __syncthreads_or(failed);
-    if (failed) break;
+    s_emax[part * kTile + pl] = em;
+    __syncthreads();
+    const int emax = max(max(s_emax[pl], s_emax[kTile + pl]), max(s_emax[2 * kTile + pl], s_emax[3 * kTile + pl]));
+    const int etau = tau_exp(emax, TI(0));
+    const int row_group = pl >> 3, row_in = pl & 7;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = part + 4 * h;
+      if (c >= NCH) continue;
+      uint32_t w[S][4];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        uint32_t d0[S], d1[S];
+        digits_of<S>(emax ? fixed_of(v[h][k], emax) : 0ll, d0);
+        digits_of<S>(emax ? fixed_of(v[h][k + 1], emax) : 0ll, d1);
+#pragma unroll
+        for (int t = 0; t < S; ++t) w[t][k / 2] = __byte_perm(d0[t], d1[t], 0x7632);
+      }
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        uint4 *dst = reinterpret_cast<uint4 *>(sA + (size_t)t * kTile * KP + ((size_t)row_group * NCH + c) * 64 +
+                                               row_in * 8);
+        *dst = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    // staging is free again: fetch the next tile while this one computes
+    if (next < P.ntiles) prefetch(next);
 
-    // ---- epilogue: rows of this pass, 16 at a time
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int r0 = 0; r0 < R; r0 += 16) {
-      uint32_t acc[L + 1][16];
+    if (warp == 0) {
+      if (lane == 0) {
+        // For digit slice s of the pencils, the operator slices t = 0..L-s are
+        // stacked along N and written from column s*R on: block t lands on the
+        // accumulator of level s + t.  The s = 0 product initialises every level.
+        const uint32_t a0 = smem_u32(sA);
+        for (int ps = 0; ps < P.passes; ++ps) {
+          const uint32_t b0 = smem_u32(sB) + ps * B_PASS_BYTES;
+          const uint32_t cbase = tmem + (uint32_t)(ps * (L + 1) * R);
 #pragma unroll
-      for (int k = 0; k <= L; ++k) {
-        const uint32_t addr = lane_base + (uint32_t)(k * R + r0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3]), "=r"(acc[k][4]),
-              "=r"(acc[k][5]), "=r"(acc[k][6]), "=r"(acc[k][7]), "=r"(acc[k][8]), "=r"(acc[k][9]),
-              "=r"(acc[k][10]), "=r"(acc[k][11]), "=r"(acc[k][12]), "=r"(acc[k][13]), "=r"(acc[k][14]),
-              "=r"(acc[k][15])
-            : "r"(addr));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (valid) {
+          for (int s = 0; s < S; ++s) {
+            const int nt = (L - s + 1) < S ? (L - s + 1) : S;  // operator slices paired with s
+            if (nt <= 0) continue;
+            const uint32_t idesc_s = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nt * R) >> 3) << 17) |
+                                     ((uint32_t)(kTile >> 4) << 24);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int r = r0 + c;
-          const int sg = r / N, i = r - sg * N;
-          const int mode = P.seg_mode[ps][sg];
-          if (mode < 0) continue;                 // rows not requested
-          if (mode != 2 && !interior) continue;   // final outputs only on interior pencils
-          long long Y = 0;
-#pragma unroll
-          for (int k = 0; k <= L; ++k) Y += (long long)acc_to_int(acc[k][c]) << (8 * (L - k));
-          const int ex = s_rowexp[ps * 48 + r] + etau - 14 - 8 * L;
-          const int oa_axis = P.axis;
-          const long long os0 = (long long)P.out_dims[1] * P.out_dims[2], os1 = P.out_dims[2];
-          const long long oa = oa_axis == 0 ? os0 : (oa_axis == 1 ? os1 : 1);
-          if (mode == 2) {
-            double *o = static_cast<double *>(P.scratch_out) + ((long long)lb * P.nf + q) * (long long)P.out_box +
-                        obase + (long long)(P.out_start[P.axis] + i) * oa;
-            *o = scaled_int_to_double(Y, ex);
-          } else {
-            const long long n3 = (long long)N * N * N;
-            const int opidx = P.seg_op[ps][sg];
-            // final output box is N^3 with transverse offsets relative to the interior
-            const long long fb = (long long)P.nf * P.nops * P.intpre[b] + ((long long)q * P.nops + opidx) * n3;
-            const long long f0 = (long long)N * N, f1 = N;
-            const long long fstr[3] = {f0, f1, 1};
-            const long long fo = fb + (long long)(t1 - P.int_lo1) * fstr[P.t1] + (long long)(t2 - P.int_lo2) * fstr[P.t2] +
-                                 (long long)i * fstr[P.axis];
-            TO *o = static_cast<TO *>(P.out) + fo;
-            if (sizeof(TO) == 8) *reinterpret_cast<double *>(o) = scaled_int_to_double(Y, ex);
-            else *reinterpret_cast<float *>(o) = scaled_int_to_float(Y, ex);
+            for (int kk = 0; kk < KP / 16; ++kk) {
+              const uint64_t da = smem_desc(a0 + (uint32_t)(s * kTile * KP * 2 + kk * 256), lbo, sbo);
+              const uint64_t db = smem_desc(b0 + (uint32_t)(kk * 256), lbo, sbo);
+              mma_bf16(cbase + (uint32_t)(s * R), da, db, idesc_s, (s == 0 && kk == 0) ? 0u : 1u);
+            }
           }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(mbar + ps)));
         }
       }
+      __syncwarp();
+    }
+
+    const bool interior = valid && P.int_lo1 <= t1 && t1 < P.int_hi1 && P.int_lo2 <= t2 && t2 < P.int_hi2;
+    for (int ps = 0; ps < P.passes; ++ps) {
+      const bool ok = mbar_wait_bounded(smem_u32(mbar + ps), ps == 0 ? phase0 : phase1);
+      if (ps == 0) phase0 ^= 1u; else phase1 ^= 1u;
+      failed = __syncthreads_or(!ok);
+      if (failed) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // ---- epilogue: this warp's quarter of the pass rows
+      const int RQ = R / 4, r0 = part * RQ;
+      const int sg = r0 / N, i0 = r0 - sg * N;
+      const int mode = P.seg_mode[ps][sg];
+      const bool wf = (mode == 0 || mode == 3) && interior;
+      const bool ws = (mode == 2 || mode == 3) && valid;
+      TO *fb = static_cast<TO *>(P.out);
+      double *sb = P.scratch_out;
+      if (wf)
+        fb += (long long)P.nf * P.nops * P.intpre[b] + ((long long)q * P.nops + P.seg_op[ps][sg]) * n3 +
+              (long long)(t1 - P.int_lo1) * f_t1 + (long long)(t2 - P.int_lo2) * f_t2;
+      if (ws)
+        sb += ((long long)lb * P.nf + q) * (long long)P.sc_box + (long long)(sc_s1 + t1) * c_t1 +
+              (long long)(sc_s2 + t2) * c_t2;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ps * (L + 1) * R + r0);
+      const int *rexp = s_rowexp + ps * 48 + r0;
+      if (RQ == 8)
+        epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0);
+      else
+        epilogue_rows<4, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    tile = next;
   }
 
   if (failed) {
     if (tid == 0) atomicExch(P.status, (int)CFD_ERR_TIMEOUT);
-    // wait (bounded) for MMAs that may still be in flight before releasing TMEM
-    const long long t0 = clock64();
-    while (clock64() - t0 < kWaitLimit / 4) {
-    }
+    mbar_wait_bounded(smem_u32(mbar), phase0);
+    mbar_wait_bounded(smem_u32(mbar + 1), phase1);
   }
+  asm volatile("cp.async.wait_all;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
@@ -497,7 +559,7 @@ cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned g
                            "cudaFuncSetAttribute");
   if (s != CFD_OK) return s;
   launch_begin(KF_DENSE, st);
-  fn<<<grid, 128, smem, st>>>(P);
+  fn<<<grid, kThreads, smem, st>>>(P);
   launch_end(KF_DENSE, st);
   return cuda_fail(cudaGetLastError(), "k_dense launch");
 }
@@ -505,10 +567,9 @@ cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned g
 template <typename TI, typename TO>
 cfd_status launch_types(const DenseParams &P, int KP, int S, int L, size_t smem, unsigned grid, cudaStream_t st) {
   switch (KP) {
-    case 16: return launch_kp<TI, TO, 16>(P, S, L, smem, grid, st);
     case 32: return launch_kp<TI, TO, 32>(P, S, L, smem, grid, st);
     case 48: return launch_kp<TI, TO, 48>(P, S, L, smem, grid, st);
-    default: set_error("dense: N + 2 ng must be at most 48"); return CFD_ERR_UNSUPPORTED;
+    default: set_error("dense: N + 2 ng must be 17..48"); return CFD_ERR_UNSUPPORTED;
   }
 }
 
@@ -594,14 +655,30 @@ namespace {
 int slices_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 5 : 2; }
 int levels_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 4 : 1; }
 
-// Shared memory per CTA; at least 80 KB so that no more than two CTAs (2 x 256
-// TMEM columns) share an SM and no CTA waits in tcgen05.alloc.
-size_t dense_smem(int KP, int S, int rows, int passes) {
-  const size_t need = (size_t)S * kTile * KP * 2 + (size_t)passes * S * rows * KP * 2 + 2 * 48 * 4 + 64 + 1024;
-  return std::max(need, (size_t)80 * 1024);
+// Shared memory per CTA: A digits, B digits of two passes, the input staging
+// tile, row exponents, exponent exchange, barriers.  At least 116 KB so that
+// one CTA (holding all 512 TMEM columns) occupies an SM.
+size_t dense_smem(int KP, int S, int rows, size_t elem) {
+  const size_t need = (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2 + (size_t)kTile * (KP + 1) * elem +
+                      (2 * 48 + 4 * kTile) * 4 + 64;
+  return std::max(need, (size_t)116 * 1024);
 }
 
 }  // namespace
+
+struct DensePlanSizes {
+  size_t gy = 0, gz = 0;  // elements per group (max over groups) of the two intermediates
+};
+
+static DensePlanSizes dense_sizes(const cfd_blocks_s *B, int nf, unsigned mask) {
+  DensePlanSizes z;
+  for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
+    const size_t N = B->sizes[gi], E = N + 2 * B->ng, nb = B->groups[gi].size();
+    if (mask & CFD_OP_DXY) z.gy = std::max(z.gy, nb * nf * N * N * E);
+    if (mask & (CFD_OP_DXZ | CFD_OP_DYZ)) z.gz = std::max(z.gz, nb * nf * N * E * E);
+  }
+  return z;
+}
 
 cfd_status dense_workspace(cfd_blocks_s *B, int nf, unsigned mask, cfd_precision prec, int n_iter, size_t *bytes) {
   if (prec != CFD_TC_BF16_EXACT && prec != CFD_TC_BF16X3) {
@@ -612,13 +689,8 @@ cfd_status dense_workspace(cfd_blocks_s *B, int nf, unsigned mask, cfd_precision
     set_error("tensor-core path: hybrid iteration is not built yet (use n_iter = 0)");
     return CFD_ERR_UNSUPPORTED;
   }
-  size_t sc = 0;
-  const bool mixed = (mask & (CFD_OP_DXY | CFD_OP_DXZ | CFD_OP_DYZ)) != 0;
-  for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
-    const size_t N = B->sizes[gi], E = N + 2 * B->ng;
-    if (mixed) sc = std::max(sc, B->groups[gi].size() * nf * E * N * N);
-  }
-  *bytes = ((sc * 8 + 255) & ~(size_t)255) + 256;
+  const DensePlanSizes z = dense_sizes(B, nf, mask);
+  *bytes = ((z.gy * 8 + 255) & ~(size_t)255) + ((z.gz * 8 + 255) & ~(size_t)255) + 256;
   return CFD_OK;
 }
 
@@ -630,8 +702,9 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
   DenseState *ds = state_of(B);
   if (!ds) { set_error("dense: operators were not built at bind"); return CFD_ERR_UNSUPPORTED; }
   const int S = slices_of(prec), L = levels_of(prec);
-  double *scratch = (double *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
-  // op order
+  const DensePlanSizes z = dense_sizes(B, nf, mask);
+  double *gy = (double *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+  double *gz = gy + ((z.gy * 8 + 255) & ~(size_t)255) / 8;
   int bits[9], nops = 0;
   for (int i = 0; i < 9; ++i)
     if (mask & (1u << i)) bits[nops++] = i;
@@ -640,9 +713,19 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       if (bits[i] == bit) return i;
     return -1;
   };
+  const bool need1 = (mask & (CFD_OP_DX | CFD_OP_DY | CFD_OP_DZ | CFD_OP_DXY | CFD_OP_DXZ | CFD_OP_DYZ)) != 0;
+  const bool need2 = (mask & (CFD_OP_DXX | CFD_OP_DYY | CFD_OP_DZZ)) != 0;
+  if ((need1 && !B->s[0].present) || (need2 && !B->s[1].present)) {
+    set_error("op needs a scheme that was not given");
+    return CFD_ERR_ARG;
+  }
+  const int sms = B->num_sms > 0 ? B->num_sms : 148;
   for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
     const DenseGroup &G = ds->groups[gi];
-    if (!G.ok) { set_error("dense: block group unsupported (uneven spacing, mixed cyclic axes or N + 2ng > 48)"); return CFD_ERR_UNSUPPORTED; }
+    if (!G.ok) {
+      set_error("dense: block group unsupported (N must be 16 or 32, uniform spacing, consistent cyclic axes)");
+      return CFD_ERR_UNSUPPORTED;
+    }
     const int N = G.N, g = B->ng, E = N + 2 * g;
     DenseParams base;
     memset(&base, 0, sizeof(base));
@@ -656,120 +739,119 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
     base.g = g;
     base.status = B->d_status;
     base.out = out;
-    base.scratch_out = scratch;
     auto run = [&](DenseParams P) -> cfd_status {
       const int np = P.n1 * P.n2;
-      const int tiles = (np + kTile - 1) / kTile;
-      const unsigned grid = (unsigned)(tiles * P.nblk * P.nf);
-      const size_t smem = dense_smem(G.Kp, S, P.rows, P.passes);
+      P.tiles_per_job = (np + kTile - 1) / kTile;
+      P.ntiles = P.tiles_per_job * P.nblk * P.nf;
+      const unsigned grid = (unsigned)std::min(P.ntiles, sms);
       const bool f32 = B->dtype == CFD_F32;
-      const bool in_scratch = !P.in_field;
-      if (in_scratch) {
+      const size_t smem = dense_smem(G.Kp, S, P.rows, (P.in_field && f32) ? 4 : 8);
+      if (!P.in_field)
         return f32 ? launch_types<double, float>(P, G.Kp, S, L, smem, grid, st)
                    : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
-      }
       return f32 ? launch_types<float, float>(P, G.Kp, S, L, smem, grid, st)
                  : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
     };
-    // ---- single-axis ops: d_a (degree 1) and d_aa (degree 2) share one tile
-    for (int box = 0; box < 3; ++box) {
-      const int bit1 = 2 - box, bit2 = 5 - box;  // dx=0,dy=1,dz=2 ; dxx=3..
-      const int o1 = opidx_of(bit1), o2 = opidx_of(bit2);
-      if (o1 < 0 && o2 < 0) continue;
-      if ((o1 >= 0 && !B->s[0].present) || (o2 >= 0 && !B->s[1].present)) {
-        set_error("op needs a scheme that was not given");
-        return CFD_ERR_ARG;
-      }
-      DenseParams P = base;
-      P.in = fields;
-      P.in_field = 1;
-      P.axis = box;
-      P.t1 = box == 0 ? 1 : 0;
-      P.t2 = box == 2 ? 1 : 2;
-      for (int t = 0; t < 3; ++t) {
-        P.in_dims[t] = E;
-        P.in_start[t] = (t == box) ? 0 : g;
-        P.out_dims[t] = N;
-        P.out_start[t] = 0;
-      }
-      P.n1 = N;
-      P.n2 = N;
-      P.int_lo1 = 0; P.int_hi1 = N; P.int_lo2 = 0; P.int_hi2 = N;
-      // passes: rows per pass <= 48 (TMEM: (L+1) x rows <= 256)
-      int segs[2][2], nsegs = 0;  // (degree, opidx)
-      if (o1 >= 0) { segs[nsegs][0] = 1; segs[nsegs][1] = o1; ++nsegs; }
-      if (o2 >= 0) { segs[nsegs][0] = 2; segs[nsegs][1] = o2; ++nsegs; }
-      const int per_pass = (nsegs * N <= 48 && (L + 1) * nsegs * N <= kTmemCols) ? nsegs : 1;
-      P.passes = nsegs / per_pass;
+    // segments: (degree, mode, op); passes of at most 32 rows
+    auto set_segments = [&](DenseParams &P, int box, int m1, int op1, int m2, int op2) {
+      int deg[2], mode[2], op[2], n = 0;
+      if (m1 >= 0) { deg[n] = 1; mode[n] = m1; op[n] = op1; ++n; }
+      if (m2 >= 0) { deg[n] = 2; mode[n] = m2; op[n] = op2; ++n; }
+      const int per_pass = (n * N <= 32) ? n : 1;
+      P.passes = n / per_pass;
       P.rows = per_pass * N;
       for (int ps = 0; ps < P.passes; ++ps) {
         P.nseg[ps] = per_pass;
         for (int k = 0; k < per_pass; ++k) {
           const int sgi = ps * per_pass + k;
-          const DenseOp &op = G.op[box][segs[sgi][0] - 1];
-          P.seg_img[ps][k] = op.img;
-          P.seg_exp[ps][k] = op.rowexp;
-          P.seg_mode[ps][k] = 0;
-          P.seg_op[ps][k] = segs[sgi][1];
+          const DenseOp &o = G.op[box][deg[sgi] - 1];
+          P.seg_img[ps][k] = o.img;
+          P.seg_exp[ps][k] = o.rowexp;
+          P.seg_mode[ps][k] = mode[sgi];
+          P.seg_op[ps][k] = op[sgi];
         }
+      }
+      return n > 0;
+    };
+    auto field_stage = [&](int box, int t1, int t2, int lo1, int n1, int lo2, int n2) {
+      DenseParams P = base;
+      P.in = fields;
+      P.in_field = 1;
+      P.axis = box;
+      P.t1 = t1;
+      P.t2 = t2;
+      for (int t = 0; t < 3; ++t) P.in_dims[t] = E;
+      P.in_start[box] = 0;
+      P.in_start[t1] = lo1;
+      P.in_start[t2] = lo2;
+      P.n1 = n1;
+      P.n2 = n2;
+      // final outputs: pencils whose transverse coordinates are interior
+      P.int_lo1 = g - lo1; P.int_hi1 = g - lo1 + N;
+      P.int_lo2 = g - lo2; P.int_hi2 = g - lo2 + N;
+      return P;
+    };
+    const int odx = opidx_of(0), ody = opidx_of(1), odz = opidx_of(2);
+    const int odxx = opidx_of(3), odyy = opidx_of(4), odzz = opidx_of(5);
+    const int odxy = opidx_of(6), odxz = opidx_of(7), odyz = opidx_of(8);
+    // S_x: D_x on interior (z, y) pencils -> d_x, d_xx
+    if (odx >= 0 || odxx >= 0) {
+      DenseParams P = field_stage(2, 0, 1, g, N, g, N);
+      set_segments(P, 2, odx >= 0 ? 0 : -1, odx, odxx >= 0 ? 0 : -1, odxx);
+      if ((s = run(P)) != CFD_OK) return s;
+    }
+    // S_y: D_y on (z interior, x extended if d_xy) -> d_y, d_yy, and G_y = D_y f for d_xy
+    if (ody >= 0 || odyy >= 0 || odxy >= 0) {
+      const bool ext = odxy >= 0;
+      DenseParams P = field_stage(1, 0, 2, g, N, ext ? 0 : g, ext ? E : N);
+      const int m1 = (ody >= 0 && ext) ? 3 : (ody >= 0 ? 0 : (ext ? 2 : -1));
+      set_segments(P, 1, m1, ody, odyy >= 0 ? 0 : -1, odyy);
+      if (ext) {
+        P.scratch_out = gy;
+        P.sc_box = (unsigned long long)N * N * E;
+        P.sc_dims[0] = N; P.sc_dims[1] = N; P.sc_dims[2] = E;
+        P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = 0;
       }
       if ((s = run(P)) != CFD_OK) return s;
     }
-    // ---- mixed ops, one order: D_i [ D_j f on rows extended along i ]
-    const int kMixed[3][3] = {{6, 2, 1}, {7, 2, 0}, {8, 1, 0}};  // bit, i (outer), j (inner) as box axes
-    for (int m = 0; m < 3; ++m) {
-      const int o = opidx_of(kMixed[m][0]);
-      if (o < 0) continue;
-      if (!B->s[0].present) { set_error("mixed ops need the first-degree scheme"); return CFD_ERR_ARG; }
-      const int ai = kMixed[m][1], aj = kMixed[m][2], ak = 3 - ai - aj;
-      DenseParams S1 = base;
-      S1.in = fields;
-      S1.in_field = 1;
-      S1.axis = aj;
-      S1.t1 = std::min(ai, ak);
-      S1.t2 = std::max(ai, ak);
-      for (int t = 0; t < 3; ++t) {
-        S1.in_dims[t] = E;
-        S1.in_start[t] = (t == ak) ? g : 0;
-        S1.out_dims[t] = (t == ai) ? E : N;
-        S1.out_start[t] = 0;
+    // S_z: D_z on (y, x) extended for d_xz / d_yz -> d_z, d_zz, and G_z = D_z f
+    if (odz >= 0 || odzz >= 0 || odxz >= 0 || odyz >= 0) {
+      const bool ext = odxz >= 0 || odyz >= 0;
+      DenseParams P = field_stage(0, 1, 2, ext ? 0 : g, ext ? E : N, ext ? 0 : g, ext ? E : N);
+      const int m1 = (odz >= 0 && ext) ? 3 : (odz >= 0 ? 0 : (ext ? 2 : -1));
+      set_segments(P, 0, m1, odz, odzz >= 0 ? 0 : -1, odzz);
+      if (ext) {
+        P.scratch_out = gz;
+        P.sc_box = (unsigned long long)N * E * E;
+        P.sc_dims[0] = N; P.sc_dims[1] = E; P.sc_dims[2] = E;
+        P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = 0;
       }
-      S1.n1 = (S1.t1 == ai) ? E : N;
-      S1.n2 = (S1.t2 == ai) ? E : N;
-      S1.int_lo1 = 0; S1.int_hi1 = S1.n1; S1.int_lo2 = 0; S1.int_hi2 = S1.n2;
-      S1.out_box = (unsigned long long)E * N * N;
-      S1.passes = 1;
-      S1.rows = N;
-      S1.nseg[0] = 1;
-      S1.seg_img[0][0] = G.op[aj][0].img;
-      S1.seg_exp[0][0] = G.op[aj][0].rowexp;
-      S1.seg_mode[0][0] = 2;
-      if ((s = run(S1)) != CFD_OK) return s;
-      DenseParams S2 = base;
-      S2.in = scratch;
-      S2.in_field = 0;
-      S2.in_box = (unsigned long long)E * N * N;
-      S2.axis = ai;
-      S2.t1 = std::min(aj, ak);
-      S2.t2 = std::max(aj, ak);
-      for (int t = 0; t < 3; ++t) {
-        S2.in_dims[t] = S1.out_dims[t];
-        S2.in_start[t] = 0;
-        S2.out_dims[t] = N;
-        S2.out_start[t] = 0;
-      }
-      S2.n1 = N;
-      S2.n2 = N;
-      S2.int_lo1 = 0; S2.int_hi1 = N; S2.int_lo2 = 0; S2.int_hi2 = N;
-      S2.passes = 1;
-      S2.rows = N;
-      S2.nseg[0] = 1;
-      S2.seg_img[0][0] = G.op[ai][0].img;
-      S2.seg_exp[0][0] = G.op[ai][0].rowexp;
-      S2.seg_mode[0][0] = 0;
-      S2.seg_op[0][0] = o;
-      if ((s = run(S2)) != CFD_OK) return s;
+      if ((s = run(P)) != CFD_OK) return s;
     }
+    // T stages on the intermediates (one order of the mixed product: the closed
+    // block operators of two axes commute, D_i D_j = D_j D_i)
+    auto scratch_stage = [&](double *src, int d0, int d1, int d2, int box, int t1, int t2, int lo1, int lo2,
+                             int op) {
+      DenseParams P = base;
+      P.in = src;
+      P.in_field = 0;
+      P.in_box = (unsigned long long)d0 * d1 * d2;
+      P.in_dims[0] = d0; P.in_dims[1] = d1; P.in_dims[2] = d2;
+      P.axis = box;
+      P.t1 = t1;
+      P.t2 = t2;
+      P.in_start[box] = 0;
+      P.in_start[t1] = lo1;
+      P.in_start[t2] = lo2;
+      P.n1 = N;
+      P.n2 = N;
+      P.int_lo1 = 0; P.int_hi1 = N; P.int_lo2 = 0; P.int_hi2 = N;
+      set_segments(P, box, 0, op, -1, -1);
+      return run(P);
+    };
+    if (odxy >= 0 && (s = scratch_stage(gy, N, N, E, 2, 0, 1, 0, 0, odxy)) != CFD_OK) return s;
+    if (odxz >= 0 && (s = scratch_stage(gz, N, E, E, 2, 0, 1, 0, g, odxz)) != CFD_OK) return s;
+    if (odyz >= 0 && (s = scratch_stage(gz, N, E, E, 1, 0, 2, 0, g, odyz)) != CFD_OK) return s;
   }
   return CFD_OK;
 }
