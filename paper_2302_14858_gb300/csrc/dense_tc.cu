@@ -280,38 +280,52 @@ __device__ __forceinline__ long long stride_of(int axis, long long s0, long long
 
 // ------------------------------------------------------------------ the kernel
 //
-// Persistent, one CTA of 16 warps per SM.  Per 128-pencil tile:
-//   all threads:  pencil values (already in shared memory) -> 5 digit rows of A
-//   all threads:  cp.async prefetch of the next tile's pencils
-//   thread 0:     tcgen05.mma for every pass, one mbarrier commit per pass
-//   all warps:    epilogue of each pass as soon as its commit arrives
-// Warp w reads TMEM lane quadrant w % 4 (pencils 32 (w % 4) .. +31), and
-// quarter w / 4 of the K chunks (splitting) or of the pass rows (epilogue).
+// Persistent, one CTA of 16 warps per SM, warp-specialised:
+//   warps 0-7   producers: cp.async the next tile's pencils into a staging
+//               buffer, split the current one into 5 digit rows of A[buf]
+//               (two A buffers), publish the pencil scales (meta_full); then
+//               thread 0 issues tcgen05.mma for every pass of the tile into
+//               one of three TMEM pass buffers (t_full on commit) and frees
+//               A[buf] with a last commit (a_empty);
+//   warps 8-15  epilogue: wait t_full, read their TMEM lanes, free the pass
+//               buffer (t_empty), rebuild the outputs and store them.
+// Every wait is bounded; a timeout latches CFD_ERR_TIMEOUT and ends the CTA.
 
 constexpr int kThreads = 512;
+constexpr int kProducers = 256;   // warps 0-7
+constexpr int kEpilogue = 256;    // warps 8-15
+constexpr int kPassCols = 160;    // TMEM columns per pass buffer ((L + 1) * R <= 160)
+constexpr int kPassBufs = 3;
 
-template <int RQ, int LEV, typename TO>
+template <int RH, int LEV, typename TO>
 __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int etau, const int *rowexp,
                                               TO *fin_base, long long fin_stride, double *sc_base,
-                                              long long sc_stride, bool write_fin, bool write_sc, int i0) {
-  uint32_t acc[LEV][RQ];
+                                              long long sc_stride, bool write_fin, bool write_sc, int i0,
+                                              uint32_t t_empty_addr) {
+  uint32_t acc[LEV][RH];
 #pragma unroll
   for (int k = 0; k < LEV; ++k) {
     const uint32_t addr = taddr + (uint32_t)k * lev_stride;
-    if constexpr (RQ == 8) {
+    if constexpr (RH == 16) {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3]), "=r"(acc[k][4]), "=r"(acc[k][5]),
+            "=r"(acc[k][6]), "=r"(acc[k][7]), "=r"(acc[k][8]), "=r"(acc[k][9]), "=r"(acc[k][10]),
+            "=r"(acc[k][11]), "=r"(acc[k][12]), "=r"(acc[k][13]), "=r"(acc[k][14]), "=r"(acc[k][15])
+          : "r"(addr));
+    } else {
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3]), "=r"(acc[k][4]),
                      "=r"(acc[k][5]), "=r"(acc[k][6]), "=r"(acc[k][7])
                    : "r"(addr));
-    } else {
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                   : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3])
-                   : "r"(addr));
     }
   }
   asm volatile("tcgen05.wait::ld.sync.aligned;");
+  // the pass buffer can be reused as soon as every epilogue thread has its values
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t_empty_addr));
 #pragma unroll
-  for (int c = 0; c < RQ; ++c) {
+  for (int c = 0; c < RH; ++c) {
     long long Y;
     if constexpr (LEV == 5) {
       const int t1 = acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]);
@@ -330,6 +344,42 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
   }
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr));
+}
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 256;"); }
+
+// Barrier of the 256 producer threads that also ORs a flag over them.
+__device__ __forceinline__ bool producer_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v));
+  return r != 0;
+}
+
+struct TileCoord {
+  int lb, q, b, t1, t2;
+  bool valid;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, int pencil) {
+  TileCoord c;
+  const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+  c.lb = job / P.nf;
+  c.q = job - c.lb * P.nf;
+  c.b = P.blocks[c.lb];
+  const int p = tj * kTile + pencil;
+  c.valid = p < P.n1 * P.n2;
+  c.t1 = c.valid ? p / P.n2 : 0;
+  c.t2 = c.valid ? p - c.t1 * P.n2 : 0;
+  return c;
+}
+
 template <typename TI, typename TO, int KP, int S, int L>
 __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -338,19 +388,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   constexpr int NCH = KP / 8;    // 8-value K chunks per pencil
   const int R = P.rows;
   const int B_PASS_BYTES = S * R * KP * 2;
-  uint16_t *sA = reinterpret_cast<uint16_t *>(smem);
-  uint16_t *sB = reinterpret_cast<uint16_t *>(smem + A_BYTES);
-  TI *stg = reinterpret_cast<TI *>(smem + A_BYTES + 2 * B_PASS_BYTES);
+  uint16_t *sA = reinterpret_cast<uint16_t *>(smem);  // [2][S][128][KP]
+  uint16_t *sB = reinterpret_cast<uint16_t *>(smem + 2 * A_BYTES);
+  TI *stg = reinterpret_cast<TI *>(smem + 2 * A_BYTES + 2 * B_PASS_BYTES);
   int *s_rowexp = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg) + kTile * PITCH * sizeof(TI));
-  int *s_emax = s_rowexp + 2 * 48;  // [4][128]
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(s_emax + 4 * kTile);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+  int *s_emax = s_rowexp + 2 * 48;   // [2][128]
+  // Pencil scales of the last 8 tiles: producers run at most 5 tiles ahead of
+  // the epilogue (two A buffers, three TMEM pass buffers), so a slot and its
+  // mbarrier phase are never reused before the epilogue has read them.
+  int *s_etau = s_emax + 2 * kTile;  // [8][128] ring
+  uint64_t *bars = reinterpret_cast<uint64_t *>(s_etau + 8 * kTile);
+  // bars: a_empty[2], t_full[3], t_empty[3], meta_full[8]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 16);
+  const uint32_t bar0 = smem_u32(bars);
+  auto a_empty = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  auto t_full = [&](int i) { return bar0 + 8u * (uint32_t)(2 + i); };
+  auto t_empty = [&](int i) { return bar0 + 8u * (uint32_t)(5 + i); };
+  auto meta_full = [&](int i) { return bar0 + 8u * (uint32_t)(8 + i); };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, part = warp >> 2;
-  const int pl = quad * 32 + lane;  // pencil within the tile == TMEM lane
   const int N = P.N, g = P.g, E = N + 2 * g;
-  const int np = P.n1 * P.n2;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -358,12 +415,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
+    for (int i = 0; i < 2; ++i) mbar_init(a_empty(i), 1);
+    for (int i = 0; i < kPassBufs; ++i) { mbar_init(t_full(i), 1); mbar_init(t_empty(i), kEpilogue); }
+    for (int i = 0; i < 8; ++i) mbar_init(meta_full(i), kProducers);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // B operand: digit images of every pass, loaded once per CTA; row exponents
-  // of pass ps at s_rowexp[ps * 48 + row].
   for (int ps = 0; ps < P.passes; ++ps) {
     for (int sg = 0; sg < P.nseg[ps]; ++sg) {
       const uint4 *src = reinterpret_cast<const uint4 *>(P.seg_img[ps][sg]);
@@ -377,117 +433,98 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       for (int i = tid; i < N; i += kThreads) s_rowexp[ps * 48 + sg * N + i] = P.seg_exp[ps][sg][i];
     }
   }
-
   const long long is0 = (long long)P.in_dims[1] * P.in_dims[2], is1 = P.in_dims[2];
   const long long s_t1 = stride_of(P.t1, is0, is1), s_t2 = stride_of(P.t2, is0, is1), s_ax = stride_of(P.axis, is0, is1);
-  const long long f_t1 = stride_of(P.t1, (long long)N * N, N), f_t2 = stride_of(P.t2, (long long)N * N, N),
-                  f_ax = stride_of(P.axis, (long long)N * N, N);
-  const long long ss0 = (long long)P.sc_dims[1] * P.sc_dims[2], ss1 = P.sc_dims[2];
-  const long long c_t1 = stride_of(P.t1, ss0, ss1), c_t2 = stride_of(P.t2, ss0, ss1), c_ax = stride_of(P.axis, ss0, ss1);
   const int in_s1 = P.t1 == 0 ? P.in_start[0] : (P.t1 == 1 ? P.in_start[1] : P.in_start[2]);
   const int in_s2 = P.t2 == 0 ? P.in_start[0] : (P.t2 == 1 ? P.in_start[1] : P.in_start[2]);
-  const int sc_s1 = P.t1 == 0 ? P.sc_start[0] : (P.t1 == 1 ? P.sc_start[1] : P.sc_start[2]);
-  const int sc_s2 = P.t2 == 0 ? P.sc_start[0] : (P.t2 == 1 ? P.sc_start[1] : P.sc_start[2]);
-  const long long n3 = (long long)N * N * N;
   const long long E3 = (long long)E * E * E;
-
-  // issue the cp.async copies of one tile's pencils into the staging buffer
-  auto prefetch = [&](int tile) {
-    const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
-    const int lb = job / P.nf, q = job - lb * P.nf;
-    const int b = P.blocks[lb];
-    const int pp = tid & (kTile - 1), jq = tid >> 7;  // pencil, first j of this thread
-    const int p = tj * kTile + pp;
-    if (p < np) {
-      const int t1 = p / P.n2, t2 = p - (p / P.n2) * P.n2;
-      long long ib = P.in_field ? (long long)P.nf * P.extpre[b] + (long long)q * E3
-                                : ((long long)lb * P.nf + q) * (long long)P.in_box;
-      ib += (long long)(in_s1 + t1) * s_t1 + (long long)(in_s2 + t2) * s_t2;
-      const TI *src = static_cast<const TI *>(P.in) + ib;
-      for (int j = jq; j < E; j += 4) {
-        if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * PITCH + j, src + (long long)j * s_ax);
-        else cp_async4(stg + pp * PITCH + j, src + (long long)j * s_ax);
-      }
-    }
-    asm volatile("cp.async.commit_group;");
-  };
-
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
-  const uint32_t lbo = 128, sbo = KP * 16;
-  uint32_t phase0 = 0, phase1 = 0;
   bool failed = false;
 
-  int tile = blockIdx.x;
-  if (tile < P.ntiles) prefetch(tile);
-  while (tile < P.ntiles && !failed) {
-    const int next = tile + gridDim.x;
-    const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
-    const int lb = job / P.nf, q = job - lb * P.nf;
-    const int b = P.blocks[lb];
-    const int p = tj * kTile + pl;
-    const bool valid = p < np;
-    const int t1 = valid ? p / P.n2 : 0, t2 = valid ? p - (p / P.n2) * P.n2 : 0;
-
-    asm volatile("cp.async.wait_all;");
-    __syncthreads();
-    // ---- split: this thread owns chunks c = part and part + 4 of pencil pl
-    TI v[2][8];
-    int em = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = part + 4 * h;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int j = c * 8 + k;
-        v[h][k] = (c < NCH && j < E && valid) ? stg[pl * PITCH + j] : TI(0);
-        em = max(em, biased_exp(v[h][k]));
+  if (warp < 8) {
+    // ================================================================ producers (+ MMA issue by thread 0)
+    const int pl = (warp & 3) * 32 + lane, half = warp >> 2;
+    auto prefetch = [&](int tile) {
+      const int pp = tid & (kTile - 1), jq = tid >> 7;  // 2 threads per pencil
+      const TileCoord c = tile_coord(P, tile, pp);
+      if (c.valid) {
+        long long ib = P.in_field ? (long long)P.nf * P.extpre[c.b] + (long long)c.q * E3
+                                  : ((long long)c.lb * P.nf + c.q) * (long long)P.in_box;
+        ib += (long long)(in_s1 + c.t1) * s_t1 + (long long)(in_s2 + c.t2) * s_t2;
+        const TI *src = static_cast<const TI *>(P.in) + ib;
+        for (int j = jq; j < E; j += 2) {
+          if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * PITCH + j, src + (long long)j * s_ax);
+          else cp_async4(stg + pp * PITCH + j, src + (long long)j * s_ax);
+        }
       }
-    }
-    s_emax[part * kTile + pl] = em;
-    __syncthreads();
-    const int emax = max(max(s_emax[pl], s_emax[kTile + pl]), max(s_emax[2 * kTile + pl], s_emax[3 * kTile + pl]));
-    const int etau = tau_exp(emax, TI(0));
-    const int row_group = pl >> 3, row_in = pl & 7;
+      asm volatile("cp.async.commit_group;");
+    };
+    const uint32_t lbo = 128, sbo = KP * 16;
+    int it = 0, pit = 0;
+    int tile = blockIdx.x;
+    if (tile < P.ntiles) prefetch(tile);
+    for (; tile < P.ntiles; tile += gridDim.x, ++it) {
+      const int buf = it & 1, use = it >> 1;
+      const TileCoord c = tile_coord(P, tile, pl);
+      asm volatile("cp.async.wait_all;");
+      producer_sync();
+      TI v[NCH / 2][8];
+      int em = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = part + 4 * h;
-      if (c >= NCH) continue;
-      uint32_t w[S][4];
+      for (int h = 0; h < NCH / 2; ++h) {
 #pragma unroll
-      for (int k = 0; k < 8; k += 2) {
-        uint32_t d0[S], d1[S];
-        digits_of<S>(emax ? fixed_of(v[h][k], emax) : 0ll, d0);
-        digits_of<S>(emax ? fixed_of(v[h][k + 1], emax) : 0ll, d1);
-#pragma unroll
-        for (int t = 0; t < S; ++t) w[t][k / 2] = __byte_perm(d0[t], d1[t], 0x7632);
+        for (int k = 0; k < 8; ++k) {
+          const int j = (half * (NCH / 2) + h) * 8 + k;
+          v[h][k] = (j < E && c.valid) ? stg[pl * PITCH + j] : TI(0);
+          em = max(em, biased_exp(v[h][k]));
+        }
       }
+      s_emax[half * kTile + pl] = em;
+      producer_sync();  // exponents exchanged, staging fully read
+      const int emax = max(s_emax[pl], s_emax[kTile + pl]);
+      if (tile + (int)gridDim.x < P.ntiles) prefetch(tile + gridDim.x);
+      // A[buf] must be free: the MMAs of its previous use have completed
+      const bool ok = use == 0 || mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1));
+      if (producer_any(!ok || failed)) { failed = true; break; }
+      if (half == 0) s_etau[(it & 7) * kTile + pl] = tau_exp(emax, TI(0));
+      uint16_t *Ab = sA + (size_t)buf * (A_BYTES / 2);
+      const int row_group = pl >> 3, row_in = pl & 7;
 #pragma unroll
-      for (int t = 0; t < S; ++t) {
-        uint4 *dst = reinterpret_cast<uint4 *>(sA + (size_t)t * kTile * KP + ((size_t)row_group * NCH + c) * 64 +
-                                               row_in * 8);
-        *dst = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      for (int h = 0; h < NCH / 2; ++h) {
+        const int ch = half * (NCH / 2) + h;
+        uint32_t w[S][4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          uint32_t d0[S], d1[S];
+          digits_of<S>(emax ? fixed_of(v[h][k], emax) : 0ll, d0);
+          digits_of<S>(emax ? fixed_of(v[h][k + 1], emax) : 0ll, d1);
+#pragma unroll
+          for (int t = 0; t < S; ++t) w[t][k / 2] = __byte_perm(d0[t], d1[t], 0x7632);
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          uint4 *dst = reinterpret_cast<uint4 *>(Ab + (size_t)t * kTile * KP + ((size_t)row_group * NCH + ch) * 64 +
+                                                 row_in * 8);
+          *dst = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+        }
       }
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // staging is free again: fetch the next tile while this one computes
-    if (next < P.ntiles) prefetch(next);
-
-    if (warp == 0) {
-      if (lane == 0) {
-        // For digit slice s of the pencils, the operator slices t = 0..L-s are
-        // stacked along N and written from column s*R on: block t lands on the
-        // accumulator of level s + t.  The s = 0 product initialises every level.
-        const uint32_t a0 = smem_u32(sA);
-        for (int ps = 0; ps < P.passes; ++ps) {
+      asm volatile("fence.proxy.async.shared::cta;");
+      mbar_arrive(meta_full(it & 7));
+      producer_sync();  // A[buf] complete
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(sA) + (uint32_t)(buf * A_BYTES);
+        for (int ps = 0; ps < P.passes; ++ps, ++pit) {
+          const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
+          if (tuse > 0 && !mbar_wait_bounded(t_empty(tb), (uint32_t)((tuse - 1) & 1))) { failed = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t b0 = smem_u32(sB) + ps * B_PASS_BYTES;
-          const uint32_t cbase = tmem + (uint32_t)(ps * (L + 1) * R);
+          const uint32_t cbase = tmem + (uint32_t)(tb * kPassCols);
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const int nt = (L - s + 1) < S ? (L - s + 1) : S;  // operator slices paired with s
+            const int nt = (L - s + 1) < S ? (L - s + 1) : S;
             if (nt <= 0) continue;
             const uint32_t idesc_s = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nt * R) >> 3) << 17) |
                                      ((uint32_t)(kTile >> 4) << 24);
@@ -499,53 +536,63 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(mbar + ps)));
+              t_full(tb)));
         }
+        if (!failed)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              a_empty(buf)));
+      } else {
+        pit += P.passes;
       }
-      __syncwarp();
     }
-
-    const bool interior = valid && P.int_lo1 <= t1 && t1 < P.int_hi1 && P.int_lo2 <= t2 && t2 < P.int_hi2;
-    for (int ps = 0; ps < P.passes; ++ps) {
-      const bool ok = mbar_wait_bounded(smem_u32(mbar + ps), ps == 0 ? phase0 : phase1);
-      if (ps == 0) phase0 ^= 1u; else phase1 ^= 1u;
-      failed = __syncthreads_or(!ok);
-      if (failed) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      // ---- epilogue: this warp's quarter of the pass rows
-      const int RQ = R / 4, r0 = part * RQ;
-      const int sg = r0 / N, i0 = r0 - sg * N;
-      const int mode = P.seg_mode[ps][sg];
-      const bool wf = (mode == 0 || mode == 3) && interior;
-      const bool ws = (mode == 2 || mode == 3) && valid;
-      TO *fb = static_cast<TO *>(P.out);
-      double *sb = P.scratch_out;
-      if (wf)
-        fb += (long long)P.nf * P.nops * P.intpre[b] + ((long long)q * P.nops + P.seg_op[ps][sg]) * n3 +
-              (long long)(t1 - P.int_lo1) * f_t1 + (long long)(t2 - P.int_lo2) * f_t2;
-      if (ws)
-        sb += ((long long)lb * P.nf + q) * (long long)P.sc_box + (long long)(sc_s1 + t1) * c_t1 +
-              (long long)(sc_s2 + t2) * c_t2;
-      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ps * (L + 1) * R + r0);
-      const int *rexp = s_rowexp + ps * 48 + r0;
-      if (RQ == 8)
-        epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0);
-      else
-        epilogue_rows<4, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0);
+    asm volatile("cp.async.wait_all;");
+  } else {
+    // ================================================================ epilogue
+    const int quad = warp & 3, ehalf = (warp - 8) >> 2;
+    const int pl = quad * 32 + lane;
+    const long long n3 = (long long)N * N * N;
+    const long long f_t1 = stride_of(P.t1, (long long)N * N, N), f_t2 = stride_of(P.t2, (long long)N * N, N),
+                    f_ax = stride_of(P.axis, (long long)N * N, N);
+    const long long ss0 = (long long)P.sc_dims[1] * P.sc_dims[2], ss1 = P.sc_dims[2];
+    const long long c_t1 = stride_of(P.t1, ss0, ss1), c_t2 = stride_of(P.t2, ss0, ss1), c_ax = stride_of(P.axis, ss0, ss1);
+    const int sc_s1 = P.t1 == 0 ? P.sc_start[0] : (P.t1 == 1 ? P.sc_start[1] : P.sc_start[2]);
+    const int sc_s2 = P.t2 == 0 ? P.sc_start[0] : (P.t2 == 1 ? P.sc_start[1] : P.sc_start[2]);
+    int it = 0, pit = 0;
+    for (int tile = blockIdx.x; tile < P.ntiles && !failed; tile += gridDim.x, ++it) {
+      const TileCoord c = tile_coord(P, tile, pl);
+      const bool interior = c.valid && P.int_lo1 <= c.t1 && c.t1 < P.int_hi1 && P.int_lo2 <= c.t2 && c.t2 < P.int_hi2;
+      if (!mbar_wait_bounded(meta_full(it & 7), (uint32_t)((it >> 3) & 1))) { failed = true; break; }
+      const int etau = s_etau[(it & 7) * kTile + pl];
+      for (int ps = 0; ps < P.passes; ++ps, ++pit) {
+        const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
+        if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1))) { failed = true; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int RH = R / 2, r0 = ehalf * RH;
+        const int sg = r0 / N, i0 = r0 - sg * N;
+        const int mode = P.seg_mode[ps][sg];
+        const bool wf = (mode == 0 || mode == 3) && interior;
+        const bool ws = (mode == 2 || mode == 3) && c.valid;
+        TO *fb = static_cast<TO *>(P.out);
+        double *sb = P.scratch_out;
+        if (wf)
+          fb += (long long)P.nf * P.nops * P.intpre[c.b] + ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
+                (long long)(c.t1 - P.int_lo1) * f_t1 + (long long)(c.t2 - P.int_lo2) * f_t2;
+        if (ws)
+          sb += ((long long)c.lb * P.nf + c.q) * (long long)P.sc_box + (long long)(sc_s1 + c.t1) * c_t1 +
+                (long long)(sc_s2 + c.t2) * c_t2;
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
+        const int *rexp = s_rowexp + ps * 48 + r0;
+        if (RH == 16)
+          epilogue_rows<16, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0, t_empty(tb));
+        else
+          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0, t_empty(tb));
+      }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    tile = next;
   }
 
-  if (failed) {
-    if (tid == 0) atomicExch(P.status, (int)CFD_ERR_TIMEOUT);
-    mbar_wait_bounded(smem_u32(mbar), phase0);
-    mbar_wait_bounded(smem_u32(mbar + 1), phase1);
-  }
-  asm volatile("cp.async.wait_all;");
+  if (failed) atomicExch(P.status, (int)CFD_ERR_TIMEOUT);
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
@@ -655,12 +702,12 @@ namespace {
 int slices_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 5 : 2; }
 int levels_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 4 : 1; }
 
-// Shared memory per CTA: A digits, B digits of two passes, the input staging
-// tile, row exponents, exponent exchange, barriers.  At least 116 KB so that
+// Shared memory per CTA: two A digit buffers, B digits of two passes, the
+// input staging tile, row exponents, exponent exchange, etau ring, barriers.  At least 116 KB so that
 // one CTA (holding all 512 TMEM columns) occupies an SM.
 size_t dense_smem(int KP, int S, int rows, size_t elem) {
-  const size_t need = (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2 + (size_t)kTile * (KP + 1) * elem +
-                      (2 * 48 + 4 * kTile) * 4 + 64;
+  const size_t need = 2 * (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2 +
+                      (size_t)kTile * (KP + 1) * elem + (2 * 48 + 2 * kTile + 8 * kTile) * 4 + 16 * 8 + 64;
   return std::max(need, (size_t)116 * 1024);
 }
 
