@@ -24,9 +24,15 @@ struct DenseParams {
   int nseg[2];               // operators (segments of N rows) per pass
   const uint16_t *seg_img[2][2];
   const int *seg_exp[2][2];
-  int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both
+  int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both, 4 halo rows
   int seg_op[2][2];          // op index in the output for final stores
   int tiles_per_job, ntiles; // 128-pencil tiles per (block, field); all tiles of the stage
+  int seg_rows;              // operator rows per segment (N, or 16 for a halo pass)
+  int kext;                  // K values loaded per pencil: N + 2g, or N + 2g + 4 with halo columns
+  const double *halo_in;     // [nblocks][nf][n1 n2][4]: previous iterate at rows 1, N-2 per degree (x dx^d)
+  double *halo_out;          // same layout, written by a halo pass (seg_mode 4)
+  const int *nbr;            // [nblocks][26] neighbour table
+  int halo_deg_mask;         // degrees whose halo columns are filled (bit d-1)
   int *status;
 };
 

@@ -132,20 +132,22 @@ uint16_t bf16_of_small_int(int a) {
   return (uint16_t)(u >> 16);
 }
 
-// Digit image of one operator: kS slices x N rows x Kp columns, canonical
-// K-major smem layout per slice: [row/8][k/8][row%8][k%8] bf16.
-void digit_image(const std::vector<ld> &D, int N, int E, int Kp, std::vector<uint16_t> &img,
+// Digit image of one operator: kS slices x rows x Kp columns (row-major D of
+// `cols` columns, cols <= Kp, rows a multiple of 8), canonical K-major smem
+// layout per slice: [row/8][k/8][row%8][k%8] bf16.  Row i is scaled by
+// 2^rowexp[i] >= max_j |D_ij|.
+void digit_image(const std::vector<ld> &D, int rows, int cols, int Kp, std::vector<uint16_t> &img,
                  std::vector<int> &rowexp) {
-  img.assign((size_t)kS * N * Kp, 0);
-  rowexp.assign(N, 0);
-  for (int i = 0; i < N; ++i) {
+  img.assign((size_t)kS * rows * Kp, 0);
+  rowexp.assign(rows, 0);
+  for (int i = 0; i < rows; ++i) {
     ld mx = 0;
-    for (int j = 0; j < E; ++j) mx = std::max(mx, fabsl(D[i * E + j]));
+    for (int j = 0; j < cols; ++j) mx = std::max(mx, fabsl(D[(size_t)i * cols + j]));
     int e = 0;
     if (mx > 0) frexpl(mx, &e);  // mx < 2^e
     rowexp[i] = e;
-    for (int j = 0; j < E; ++j) {
-      long long F = llrintl(ldexpl(D[i * E + j], 39 - e));  // |F| <= 2^39
+    for (int j = 0; j < cols; ++j) {
+      long long F = llrintl(ldexpl(D[(size_t)i * cols + j], 39 - e));  // |F| <= 2^39
       int dig[kS];
       for (int t = kS - 1; t >= 1; --t) {
         long long r = F & 0xFF;
@@ -155,10 +157,57 @@ void digit_image(const std::vector<ld> &D, int N, int E, int Kp, std::vector<uin
       }
       dig[0] = (int)F;
       for (int t = 0; t < kS; ++t) {
-        const size_t off = (size_t)t * N * Kp + ((size_t)(i / 8) * (Kp / 8) + j / 8) * 64 + (i % 8) * 8 + (j % 8);
+        const size_t off = (size_t)t * rows * Kp + ((size_t)(i / 8) * (Kp / 8) + j / 8) * 64 + (i % 8) * 8 + (j % 8);
         img[off] = bf16_of_small_int(dig[t]);
       }
     }
+  }
+}
+
+// Iterated block system of Eq. iter_center_P in dense form (no dx scaling):
+// unknowns k = -1..N with the derivative fixed at k = -2 (d_lo) and k = N+1
+// (d_hi);  d[k] = sum_j D1[k][j] f_j + cm[k] d_lo + cp[k] d_hi for k = 0..N-1.
+void iterated_operator(const SchemeCoef &s, int N, int g, std::vector<ld> &D1, std::vector<ld> &cm,
+                       std::vector<ld> &cp) {
+  const int E = N + 2 * g, n = N + 2;
+  std::vector<ld> A(n * n, 0), Bm(n * E, 0), Ic(n * 2, 0);
+  for (int r = 0; r < n; ++r) {
+    const int k = r - 1;
+    A[r * n + r] = 1;
+    if (r > 0) A[r * n + r - 1] = s.a;
+    if (r < n - 1) A[r * n + r + 1] = s.a;
+    for (int m = -s.M; m <= s.M; ++m) Bm[r * E + k + m + g] = s.rhs[m + s.M];
+  }
+  Ic[0 * 2 + 0] = -s.a;          // row k = -1 carries -a d_lo
+  Ic[(n - 1) * 2 + 1] = -s.a;    // row k = N carries -a d_hi
+  for (int c = 0; c < n; ++c)
+    for (int r = c + 1; r < n; ++r) {
+      const ld f = A[r * n + c] / A[c * n + c];
+      if (f == 0) continue;
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      for (int k = 0; k < E; ++k) Bm[r * E + k] -= f * Bm[c * E + k];
+      for (int k = 0; k < 2; ++k) Ic[r * 2 + k] -= f * Ic[c * 2 + k];
+    }
+  std::vector<ld> X(n * E), Y(n * 2);
+  for (int r = n - 1; r >= 0; --r) {
+    for (int k = 0; k < E; ++k) {
+      ld v = Bm[r * E + k];
+      for (int q = r + 1; q < n; ++q) v -= A[r * n + q] * X[q * E + k];
+      X[r * E + k] = v / A[r * n + r];
+    }
+    for (int k = 0; k < 2; ++k) {
+      ld v = Ic[r * 2 + k];
+      for (int q = r + 1; q < n; ++q) v -= A[r * n + q] * Y[q * 2 + k];
+      Y[r * 2 + k] = v / A[r * n + r];
+    }
+  }
+  D1.assign(N * E, 0);
+  cm.assign(N, 0);
+  cp.assign(N, 0);
+  for (int k = 0; k < N; ++k) {
+    for (int j = 0; j < E; ++j) D1[k * E + j] = X[(k + 1) * E + j];
+    cm[k] = Y[(k + 1) * 2 + 0];
+    cp[k] = Y[(k + 1) * 2 + 1];
   }
 }
 
@@ -301,7 +350,7 @@ template <int RH, int LEV, typename TO>
 __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int etau, const int *rowexp,
                                               TO *fin_base, long long fin_stride, double *sc_base,
                                               long long sc_stride, bool write_fin, bool write_sc, int i0,
-                                              uint32_t t_empty_addr) {
+                                              uint32_t t_empty_addr, int sc_rows) {
   uint32_t acc[LEV][RH];
 #pragma unroll
   for (int k = 0; k < LEV; ++k) {
@@ -340,7 +389,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
       if constexpr (sizeof(TO) == 8) fin_base[i * fin_stride] = scaled_int_to_double(Y, ex);
       else fin_base[i * fin_stride] = scaled_int_to_float(Y, ex);
     }
-    if (write_sc) sc_base[i * sc_stride] = scaled_int_to_double(Y, ex);
+    if (write_sc && i < sc_rows) sc_base[i * sc_stride] = scaled_int_to_double(Y, ex);
   }
 }
 
@@ -366,6 +415,17 @@ struct TileCoord {
   int lb, q, b, t1, t2;
   bool valid;
 };
+
+__device__ __forceinline__ int dir_index_dev(int dz, int dy, int dx) {
+  const int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
+  return r > 13 ? r - 1 : r;
+}
+
+// pencil index p (within the block and field) of pencil `pencil` of a tile
+__device__ __forceinline__ int tile_pencil(const DenseParams &P, int tile, int pencil) {
+  const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+  return tj * kTile + pencil;
+}
 
 __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, int pencil) {
   TileCoord c;
@@ -420,17 +480,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
     for (int i = 0; i < 8; ++i) mbar_init(meta_full(i), kProducers);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  const int SR = P.seg_rows;
   for (int ps = 0; ps < P.passes; ++ps) {
     for (int sg = 0; sg < P.nseg[ps]; ++sg) {
       const uint4 *src = reinterpret_cast<const uint4 *>(P.seg_img[ps][sg]);
-      const int slice_u4 = N * KP * 2 / 16;
+      const int slice_u4 = SR * KP * 2 / 16;
       for (int t = 0; t < S; ++t) {
         uint4 *dst = reinterpret_cast<uint4 *>(sB + (size_t)ps * (B_PASS_BYTES / 2) + (size_t)t * R * KP +
-                                               (size_t)sg * N * KP);
+                                               (size_t)sg * SR * KP);
         const uint4 *sp = src + (size_t)t * slice_u4;
         for (int i = tid; i < slice_u4; i += kThreads) dst[i] = __ldg(sp + i);
       }
-      for (int i = tid; i < N; i += kThreads) s_rowexp[ps * 48 + sg * N + i] = P.seg_exp[ps][sg][i];
+      for (int i = tid; i < SR; i += kThreads) s_rowexp[ps * 48 + sg * SR + i] = P.seg_exp[ps][sg][i];
     }
   }
   const long long is0 = (long long)P.in_dims[1] * P.in_dims[2], is1 = P.in_dims[2];
@@ -458,6 +519,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
           if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * PITCH + j, src + (long long)j * s_ax);
           else cp_async4(stg + pp * PITCH + j, src + (long long)j * s_ax);
         }
+        if (P.halo_in) {
+          // previous iterate of the neighbours at k^c: d_lo from the lower neighbour's row N-2,
+          // d_hi from the upper neighbour's row 1 (same pencil), per degree
+          const int ez = P.axis == 0, ey = P.axis == 1, ex = P.axis == 2;
+          const int nb = P.nbr[c.b * 26 + dir_index_dev(jq ? ez : -ez, jq ? ey : -ey, jq ? ex : -ex)];
+          const long long hp = ((long long)nb * P.nf + c.q) * (long long)(P.n1 * P.n2) +
+                               (long long)(tile_pencil(P, tile, pp));
+          for (int d = 0; d < 2; ++d) {
+            const double hv = ((P.halo_deg_mask >> d) & 1) ? P.halo_in[hp * 4 + 2 * d + (jq ? 0 : 1)] : 0.0;
+            stg[pp * PITCH + E + 2 * d + jq] = TI(hv);
+          }
+        }
       }
       asm volatile("cp.async.commit_group;");
     };
@@ -477,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int j = (half * (NCH / 2) + h) * 8 + k;
-          v[h][k] = (j < E && c.valid) ? stg[pl * PITCH + j] : TI(0);
+          v[h][k] = (j < P.kext && c.valid) ? stg[pl * PITCH + j] : TI(0);
           em = max(em, biased_exp(v[h][k]));
         }
       }
@@ -568,24 +641,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
         if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1))) { failed = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int RH = R / 2, r0 = ehalf * RH;
-        const int sg = r0 / N, i0 = r0 - sg * N;
+        const int sg = r0 / P.seg_rows, i0 = r0 - sg * P.seg_rows;
         const int mode = P.seg_mode[ps][sg];
         const bool wf = (mode == 0 || mode == 3) && interior;
-        const bool ws = (mode == 2 || mode == 3) && c.valid;
+        // mode 4 (halo pass): rows 0-3 of the first half go to the pencil's 4 halo values
+        const bool halo = mode == 4;
+        const bool ws = (mode == 2 || mode == 3 || (halo && ehalf == 0)) && c.valid;
         TO *fb = static_cast<TO *>(P.out);
         double *sb = P.scratch_out;
         if (wf)
           fb += (long long)P.nf * P.nops * P.intpre[c.b] + ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
                 (long long)(c.t1 - P.int_lo1) * f_t1 + (long long)(c.t2 - P.int_lo2) * f_t2;
-        if (ws)
+        if (ws && halo)
+          sb = P.halo_out + (((long long)c.b * P.nf + c.q) * (long long)(P.n1 * P.n2) + tile_pencil(P, tile, pl)) * 4;
+        else if (ws)
           sb += ((long long)c.lb * P.nf + c.q) * (long long)P.sc_box + (long long)(sc_s1 + c.t1) * c_t1 +
                 (long long)(sc_s2 + c.t2) * c_t2;
+        const long long sstr = halo ? 1 : c_ax;
+        const int srows = halo ? 4 : 1 << 30;
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
         const int *rexp = s_rowexp + ps * 48 + r0;
         if (RH == 16)
-          epilogue_rows<16, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0, t_empty(tb));
+          epilogue_rows<16, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows);
         else
-          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, c_ax, wf, ws, i0, t_empty(tb));
+          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows);
       }
     }
   }
@@ -630,7 +709,12 @@ struct DenseOp {        // one (group, axis, degree) operator
 struct DenseGroup {
   int N = 0, Kp = 0;
   bool ok = false;
-  DenseOp op[3][2];    // [axis box index z,y,x][degree-1]
+  bool iter_ok = false;  // iterated images built (E + 4 <= Kp)
+  bool cyc[3] = {false, false, false};
+  DenseOp op[3][2];      // [axis box index z,y,x][degree-1]: closed operator [0]D, dx-scaled
+  DenseOp opI[3][2];     // iterated operator [D1 | c- | c+] with halo columns, dx-scaled
+  DenseOp halo0[3];      // rows 1 and N-2 of [0]D per degree (16 rows), unscaled
+  DenseOp haloI[3];      // rows 1 and N-2 of the iterated operator (16 rows), unscaled
 };
 
 struct DenseState {
@@ -641,59 +725,94 @@ DenseState *state_of(cfd_blocks_s *B) { return reinterpret_cast<DenseState *>(B-
 
 }  // namespace
 
+static cfd_status upload_op(cfd_blocks_s *B, const std::vector<ld> &D, int rows, int cols, int Kp, DenseOp &o) {
+  std::vector<uint16_t> img;
+  std::vector<int> rexp;
+  digit_image(D, rows, cols, Kp, img, rexp);
+  cfd_status s = cuda_fail(cudaMalloc((void **)&o.img, img.size() * 2), "cudaMalloc");
+  if (s == CFD_OK) s = cuda_fail(cudaMemcpy(o.img, img.data(), img.size() * 2, cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (s == CFD_OK) s = cuda_fail(cudaMalloc((void **)&o.rowexp, rexp.size() * 4), "cudaMalloc");
+  if (s == CFD_OK) s = cuda_fail(cudaMemcpy(o.rowexp, rexp.data(), rexp.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (o.img) B->d_dense_ptrs.push_back(o.img);
+  if (o.rowexp) B->d_dense_ptrs.push_back(o.rowexp);
+  return s;
+}
+
 cfd_status dense_bind(cfd_blocks_s *B) {
   // The dense state lives in host memory; its device images are freed with the handle.
   DenseState *st = new (std::nothrow) DenseState();
   if (!st) { set_error("out of host memory"); return CFD_ERR_ALLOC; }
+  B->dense_state = st;
+  B->dense_free = [](void *p) { delete reinterpret_cast<DenseState *>(p); };
   const int g = B->ng;
   for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
     DenseGroup G;
     G.N = B->sizes[gi];
-    const int E = G.N + 2 * g;
+    const int N = G.N, E = N + 2 * g;
     G.Kp = (E + 15) / 16 * 16;
-    G.ok = G.Kp <= 48 && (G.N == 16 || G.N == 32);
+    G.ok = G.Kp <= 48 && (N == 16 || N == 32);
+    G.iter_ok = G.ok && E + 4 <= G.Kp;
     const int b0 = B->groups[gi][0];
     for (int b : B->groups[gi])
       for (int a = 0; a < 3; ++a)
         if (B->dx[b * 3 + a] != B->dx[b0 * 3 + a]) G.ok = false;
-    if (G.ok) {
-      for (int box = 0; box < 3; ++box) {
-        const int ax = 2 - box;  // dx index (x, y, z)
-        // cyclic along this axis if every block of the group is its own neighbour on both faces
-        int ncyc = 0;
-        const int ez = box == 0, ey = box == 1, ex = box == 2;
-        for (int b : B->groups[gi]) {
-          auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
-          const int lo = B->nbr[b * 26 + di(-ez, -ey, -ex)], hi = B->nbr[b * 26 + di(ez, ey, ex)];
-          if (lo == b && hi == b) ++ncyc;
+    for (int box = 0; box < 3 && G.ok; ++box) {
+      const int ax = 2 - box;  // dx index (x, y, z)
+      // cyclic along this axis if every block of the group is its own neighbour on both faces
+      int ncyc = 0;
+      const int ez = box == 0, ey = box == 1, ex = box == 2;
+      for (int b : B->groups[gi]) {
+        auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
+        const int lo = B->nbr[b * 26 + di(-ez, -ey, -ex)], hi = B->nbr[b * 26 + di(ez, ey, ex)];
+        if (lo == b && hi == b) ++ncyc;
+      }
+      const bool cyc = ncyc == (int)B->groups[gi].size();
+      if (ncyc && !cyc) { G.ok = false; break; }
+      G.cyc[box] = cyc;
+      std::vector<ld> H0(16 * E, 0), HI(16 * G.Kp, 0);
+      for (int d = 1; d <= 2; ++d) {
+        if (!B->s[d - 1].present) continue;
+        const ld h = B->dx[b0 * 3 + ax];
+        const ld scale = 1.0L / (d == 1 ? h : h * h);
+        std::vector<ld> D;
+        if (cyc) cyclic_operator(B->s[d - 1], N, g, scale, D);
+        else closed_operator(B->s[d - 1], N, g, scale, D);
+        cfd_status s = upload_op(B, D, N, E, G.Kp, G.op[box][d - 1]);
+        if (s != CFD_OK) return s;
+        if (cyc || !G.iter_ok) continue;
+        // closed operator without dx scaling: rows 1 and N-2 feed the first halo pass
+        std::vector<ld> D0;
+        closed_operator(B->s[d - 1], N, g, 1.0L, D0);
+        for (int j = 0; j < E; ++j) {
+          H0[(2 * (d - 1)) * E + j] = D0[1 * E + j];
+          H0[(2 * (d - 1) + 1) * E + j] = D0[(N - 2) * E + j];
         }
-        const bool cyc = ncyc == (int)B->groups[gi].size();
-        if (ncyc && !cyc) G.ok = false;
-        for (int d = 1; d <= 2; ++d) {
-          if (!B->s[d - 1].present || !G.ok) continue;
-          const ld h = B->dx[b0 * 3 + ax];
-          const ld scale = 1.0L / (d == 1 ? h : h * h);
-          std::vector<ld> D;
-          if (cyc) cyclic_operator(B->s[d - 1], G.N, g, scale, D);
-          else closed_operator(B->s[d - 1], G.N, g, scale, D);
-          std::vector<uint16_t> img;
-          std::vector<int> rexp;
-          digit_image(D, G.N, E, G.Kp, img, rexp);
-          DenseOp &o = G.op[box][d - 1];
-          cfd_status s = cuda_fail(cudaMalloc((void **)&o.img, img.size() * 2), "cudaMalloc");
-          if (s == CFD_OK) s = cuda_fail(cudaMemcpy(o.img, img.data(), img.size() * 2, cudaMemcpyHostToDevice), "cudaMemcpy");
-          if (s == CFD_OK) s = cuda_fail(cudaMalloc((void **)&o.rowexp, rexp.size() * 4), "cudaMalloc");
-          if (s == CFD_OK) s = cuda_fail(cudaMemcpy(o.rowexp, rexp.data(), rexp.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-          if (o.img) B->d_dense_ptrs.push_back(o.img);
-          if (o.rowexp) B->d_dense_ptrs.push_back(o.rowexp);
-          if (s != CFD_OK) { delete st; return s; }
+        std::vector<ld> D1, cm, cp;
+        iterated_operator(B->s[d - 1], N, g, D1, cm, cp);
+        const int hc = E + 2 * (d - 1);  // halo columns of this degree
+        std::vector<ld> F(N * G.Kp, 0);
+        for (int i = 0; i < N; ++i) {
+          for (int j = 0; j < E; ++j) F[i * G.Kp + j] = D1[i * E + j] * scale;
+          F[i * G.Kp + hc] = cm[i] * scale;
+          F[i * G.Kp + hc + 1] = cp[i] * scale;
         }
+        if ((s = upload_op(B, F, N, G.Kp, G.Kp, G.opI[box][d - 1])) != CFD_OK) return s;
+        const int rows[2] = {1, N - 2};
+        for (int w = 0; w < 2; ++w) {
+          const int r = 2 * (d - 1) + w, i = rows[w];
+          for (int j = 0; j < E; ++j) HI[r * G.Kp + j] = D1[i * E + j];
+          HI[r * G.Kp + hc] = cm[i];
+          HI[r * G.Kp + hc + 1] = cp[i];
+        }
+      }
+      if (!cyc && G.iter_ok) {
+        cfd_status s = upload_op(B, H0, 16, E, G.Kp, G.halo0[box]);
+        if (s == CFD_OK) s = upload_op(B, HI, 16, G.Kp, G.Kp, G.haloI[box]);
+        if (s != CFD_OK) return s;
       }
     }
     st->groups.push_back(G);
   }
-  B->dense_state = st;
-  B->dense_free = [](void *p) { delete reinterpret_cast<DenseState *>(p); };
   return CFD_OK;
 }
 
@@ -715,14 +834,19 @@ size_t dense_smem(int KP, int S, int rows, size_t elem) {
 
 struct DensePlanSizes {
   size_t gy = 0, gz = 0;  // elements per group (max over groups) of the two intermediates
+  size_t halo = 0;        // elements of one halo buffer (two are used, ping-pong)
 };
 
-static DensePlanSizes dense_sizes(const cfd_blocks_s *B, int nf, unsigned mask) {
+static size_t bytes256(size_t elems) { return (elems * 8 + 255) & ~(size_t)255; }
+
+static DensePlanSizes dense_sizes(const cfd_blocks_s *B, int nf, unsigned mask, int n_iter) {
   DensePlanSizes z;
   for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
     const size_t N = B->sizes[gi], E = N + 2 * B->ng, nb = B->groups[gi].size();
     if (mask & CFD_OP_DXY) z.gy = std::max(z.gy, nb * nf * N * N * E);
     if (mask & (CFD_OP_DXZ | CFD_OP_DYZ)) z.gz = std::max(z.gz, nb * nf * N * E * E);
+    // halo values are indexed by global block id and the pencil of the stage (at most E^2 pencils)
+    if (n_iter > 0) z.halo = std::max(z.halo, (size_t)B->nblocks * nf * E * E * 4);
   }
   return z;
 }
@@ -732,12 +856,8 @@ cfd_status dense_workspace(cfd_blocks_s *B, int nf, unsigned mask, cfd_precision
     set_error("tensor-core precision not available (TF32 is not built)");
     return CFD_ERR_UNSUPPORTED;
   }
-  if (n_iter != 0) {
-    set_error("tensor-core path: hybrid iteration is not built yet (use n_iter = 0)");
-    return CFD_ERR_UNSUPPORTED;
-  }
-  const DensePlanSizes z = dense_sizes(B, nf, mask);
-  *bytes = ((z.gy * 8 + 255) & ~(size_t)255) + ((z.gz * 8 + 255) & ~(size_t)255) + 256;
+  const DensePlanSizes z = dense_sizes(B, nf, mask, n_iter);
+  *bytes = bytes256(z.gy) + bytes256(z.gz) + 2 * bytes256(z.halo) + 256;
   return CFD_OK;
 }
 
@@ -749,9 +869,10 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
   DenseState *ds = state_of(B);
   if (!ds) { set_error("dense: operators were not built at bind"); return CFD_ERR_UNSUPPORTED; }
   const int S = slices_of(prec), L = levels_of(prec);
-  const DensePlanSizes z = dense_sizes(B, nf, mask);
+  const DensePlanSizes z = dense_sizes(B, nf, mask, n_iter);
   double *gy = (double *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
-  double *gz = gy + ((z.gy * 8 + 255) & ~(size_t)255) / 8;
+  double *gz = gy + bytes256(z.gy) / 8;
+  double *halo[2] = {gz + bytes256(z.gz) / 8, gz + bytes256(z.gz) / 8 + bytes256(z.halo) / 8};
   int bits[9], nops = 0;
   for (int i = 0; i < 9; ++i)
     if (mask & (1u << i)) bits[nops++] = i;
@@ -774,6 +895,10 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       return CFD_ERR_UNSUPPORTED;
     }
     const int N = G.N, g = B->ng, E = N + 2 * g;
+    if (n_iter > 0 && !G.iter_ok) {
+      set_error("dense: hybrid iteration needs N + 2 ng + 4 <= the padded K of the block size");
+      return CFD_ERR_UNSUPPORTED;
+    }
     DenseParams base;
     memset(&base, 0, sizeof(base));
     base.blocks = B->d_groups[gi];
@@ -786,6 +911,10 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
     base.g = g;
     base.status = B->d_status;
     base.out = out;
+    base.seg_rows = N;
+    base.kext = E;
+    base.nbr = B->d_nbr;
+    base.halo_deg_mask = (B->s[0].present ? 1 : 0) | (B->s[1].present ? 2 : 0);
     auto run = [&](DenseParams P) -> cfd_status {
       const int np = P.n1 * P.n2;
       P.tiles_per_job = (np + kTile - 1) / kTile;
@@ -800,6 +929,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
                  : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
     };
     // segments: (degree, mode, op); passes of at most 32 rows
+    auto iterating = [&](int box) { return n_iter > 0 && !G.cyc[box]; };
     auto set_segments = [&](DenseParams &P, int box, int m1, int op1, int m2, int op2) {
       int deg[2], mode[2], op[2], n = 0;
       if (m1 >= 0) { deg[n] = 1; mode[n] = m1; op[n] = op1; ++n; }
@@ -811,7 +941,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.nseg[ps] = per_pass;
         for (int k = 0; k < per_pass; ++k) {
           const int sgi = ps * per_pass + k;
-          const DenseOp &o = G.op[box][deg[sgi] - 1];
+          const DenseOp &o = iterating(box) ? G.opI[box][deg[sgi] - 1] : G.op[box][deg[sgi] - 1];
           P.seg_img[ps][k] = o.img;
           P.seg_exp[ps][k] = o.rowexp;
           P.seg_mode[ps][k] = mode[sgi];
@@ -819,6 +949,37 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         }
       }
       return n > 0;
+    };
+    // A stage along a decomposed axis with n_iter > 0 (Eq. iter_center_P): halo
+    // passes compute rows 1 and N-2 of every block's iterate [0], [1], ...
+    // [n_iter-1] (the values the neighbours need at their k^c nodes) into a
+    // ping-pong buffer; the final pass applies the iterated operator with
+    // those values as four extra K columns.  Each pass is one launch: all
+    // blocks of iterate i are complete before any block reads them.
+    auto run_stage = [&](DenseParams P, int box) -> cfd_status {
+      if (!iterating(box)) return run(P);
+      DenseParams H = P;
+      H.passes = 1;
+      H.rows = 16;
+      H.seg_rows = 16;
+      H.nseg[0] = 1;
+      H.nseg[1] = 0;
+      H.seg_mode[0][0] = 4;
+      H.seg_op[0][0] = 0;
+      H.scratch_out = nullptr;
+      for (int it = 0; it < n_iter; ++it) {
+        const DenseOp &o = it == 0 ? G.halo0[box] : G.haloI[box];
+        H.seg_img[0][0] = o.img;
+        H.seg_exp[0][0] = o.rowexp;
+        H.halo_in = it == 0 ? nullptr : halo[(it - 1) & 1];
+        H.halo_out = halo[it & 1];
+        H.kext = it == 0 ? E : E + 4;
+        cfd_status r = run(H);
+        if (r != CFD_OK) return r;
+      }
+      P.halo_in = halo[(n_iter - 1) & 1];
+      P.kext = E + 4;
+      return run(P);
     };
     auto field_stage = [&](int box, int t1, int t2, int lo1, int n1, int lo2, int n2) {
       DenseParams P = base;
@@ -845,7 +1006,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
     if (odx >= 0 || odxx >= 0) {
       DenseParams P = field_stage(2, 0, 1, g, N, g, N);
       set_segments(P, 2, odx >= 0 ? 0 : -1, odx, odxx >= 0 ? 0 : -1, odxx);
-      if ((s = run(P)) != CFD_OK) return s;
+      if ((s = run_stage(P, 2)) != CFD_OK) return s;
     }
     // S_y: D_y on (z interior, x extended if d_xy) -> d_y, d_yy, and G_y = D_y f for d_xy
     if (ody >= 0 || odyy >= 0 || odxy >= 0) {
@@ -859,7 +1020,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.sc_dims[0] = N; P.sc_dims[1] = N; P.sc_dims[2] = E;
         P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = 0;
       }
-      if ((s = run(P)) != CFD_OK) return s;
+      if ((s = run_stage(P, 1)) != CFD_OK) return s;
     }
     // S_z: D_z on (y, x) extended for d_xz / d_yz -> d_z, d_zz, and G_z = D_z f
     if (odz >= 0 || odzz >= 0 || odxz >= 0 || odyz >= 0) {
@@ -873,7 +1034,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.sc_dims[0] = N; P.sc_dims[1] = E; P.sc_dims[2] = E;
         P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = 0;
       }
-      if ((s = run(P)) != CFD_OK) return s;
+      if ((s = run_stage(P, 0)) != CFD_OK) return s;
     }
     // T stages on the intermediates (one order of the mixed product: the closed
     // block operators of two axes commute, D_i D_j = D_j D_i)
@@ -894,7 +1055,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       P.n2 = N;
       P.int_lo1 = 0; P.int_hi1 = N; P.int_lo2 = 0; P.int_hi2 = N;
       set_segments(P, box, 0, op, -1, -1);
-      return run(P);
+      return run_stage(P, box);
     };
     if (odxy >= 0 && (s = scratch_stage(gy, N, N, E, 2, 0, 1, 0, 0, odxy)) != CFD_OK) return s;
     if (odxz >= 0 && (s = scratch_stage(gz, N, E, E, 2, 0, 1, 0, g, odxz)) != CFD_OK) return s;

@@ -85,6 +85,58 @@ def test_exact_slices_all_ops(lib, torch, NM, N):
         assert v < TOL_EXACT64, (k, v)
 
 
+@pytest.mark.parametrize("NM,N,n_iter,nf", [(64, 16, 1, 4), (64, 16, 2, 2), (64, 32, 1, 2), (128, 32, 2, 1)])
+def test_exact_slices_hybrid_iteration(lib, torch, NM, N, n_iter, nf):
+    """Eq. iter_center_P on the tensor cores: halo passes + iterated operator vs the oracle."""
+    g = 4
+    r = W.rng(500 + NM + N + n_iter)
+    fs = [W.sine_sum(r, 8, 1, 12) for _ in range(nf)]  # non-zero on every block face
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    got = apply(lib, torch, B, buf, nf, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, n_iter).reshape(
+        mesh.nblocks, nf, 9, N, N, N)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = {}
+    for q in range(nf):
+        ref = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, n_iter)
+        closed = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, 0)
+        for i, op in enumerate(OPS):
+            worst[(q, op)] = rel_max(got[:, q, i], ref[op].reshape(mesh.nblocks, N, N, N))
+        # the iteration moves the result far beyond the tolerance, so the comparison can tell
+        assert max(rel_max(closed[op], ref[op]) for op in OPS) > 10 * TOL_EXACT64
+    print("iterated exact-slice max rel err", max(worst.values()))
+    for k, v in worst.items():
+        assert v < TOL_EXACT64, (k, v)
+
+
+def test_exact_slices_iteration_matches_banded_full_size(lib, torch):
+    """128^3 as 512 blocks of 16^3, one hybrid iteration: tensor cores vs the FP64 banded solve."""
+    NM, N, g = 128, 16, 4
+    fs = fields4(2302 + 5)
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    tc = apply(lib, torch, B, buf, 4, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 1).reshape(mesh.nblocks, 4, 9, -1)
+    fp = apply(lib, torch, B, buf, 4, lib.CFD_OP_ALL, lib.CFD_FP64_BANDED, 1).reshape(mesh.nblocks, 4, 9, -1)
+    errs = [rel_max(tc[:, q, i], fp[:, q, i]) for q in range(4) for i in range(9)]
+    print("iterated tc vs fp64 banded max rel err", max(errs))
+    assert max(errs) < TOL_EXACT64
+
+
+def test_exact_slices_iteration_periodic_block_is_cyclic(lib, torch):
+    """A single periodic block has no decomposed axis: n_iter leaves the cyclic result unchanged."""
+    NM = N = 16
+    g = 4
+    fs = fields4(91)[:1]
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    a = apply(lib, torch, B, buf, 1, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 0)
+    b = apply(lib, torch, B, buf, 1, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 2)
+    assert np.array_equal(a, b)
+
+
 def test_exact_slices_match_banded_fp64_full_size(lib, torch):
     """128^3 as 512 blocks of 16^3, 4 fields, 9 ops: tensor-core vs the GPU FP64 banded solve."""
     NM, N, g = 128, 16, 4
