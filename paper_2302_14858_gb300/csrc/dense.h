@@ -33,6 +33,8 @@ struct DenseParams {
   double *halo_out;          // same layout, written by a halo pass (seg_mode 4)
   const int *nbr;            // [nblocks][26] neighbour table
   int halo_deg_mask;         // degrees whose halo columns are filled (bit d-1)
+  int xrow;                  // x-axis stage with 16-byte aligned pencil rows: chunked row copies
+  int xvec;                  // x-axis stage with a 16-byte aligned output: vector stores
   int *status;
 };
 

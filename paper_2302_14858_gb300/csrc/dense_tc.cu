@@ -319,6 +319,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t p
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src));
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
+}
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
 }
@@ -350,7 +353,7 @@ template <int RH, int LEV, typename TO>
 __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int etau, const int *rowexp,
                                               TO *fin_base, long long fin_stride, double *sc_base,
                                               long long sc_stride, bool write_fin, bool write_sc, int i0,
-                                              uint32_t t_empty_addr, int sc_rows) {
+                                              uint32_t t_empty_addr, int sc_rows, bool vec) {
   uint32_t acc[LEV][RH];
 #pragma unroll
   for (int k = 0; k < LEV; ++k) {
@@ -373,23 +376,41 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
   // the pass buffer can be reused as soon as every epilogue thread has its values
   asm volatile("tcgen05.fence::before_thread_sync;");
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t_empty_addr));
+  // 16-byte vector stores where the output axis is contiguous (x): pencil rows are
+  // 16-byte aligned (N and the output offsets are multiples of 16 elements)
+  constexpr int V = 16 / sizeof(TO);
 #pragma unroll
-  for (int c = 0; c < RH; ++c) {
-    long long Y;
-    if constexpr (LEV == 5) {
-      const int t1 = acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]);
-      const int t2 = acc_to_int(acc[2][c]) * 256 + acc_to_int(acc[3][c]);
-      Y = ((long long)t1 << 24) + ((long long)t2 << 8) + (long long)acc_to_int(acc[4][c]);
-    } else {
-      Y = (long long)(acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]));
+  for (int c0 = 0; c0 < RH; c0 += V) {
+    TO o[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int c = c0 + u;
+      long long Y;
+      if constexpr (LEV == 5) {
+        const int t1 = acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]);
+        const int t2 = acc_to_int(acc[2][c]) * 256 + acc_to_int(acc[3][c]);
+        Y = ((long long)t1 << 24) + ((long long)t2 << 8) + (long long)acc_to_int(acc[4][c]);
+      } else {
+        Y = (long long)(acc_to_int(acc[0][c]) * 256 + acc_to_int(acc[1][c]));
+      }
+      const int ex = rowexp[c] + etau - 14 - 8 * (LEV - 1);
+      const long long i = i0 + c;
+      if constexpr (sizeof(TO) == 8) {
+        const double dv = scaled_int_to_double(Y, ex);
+        o[u] = dv;
+        if (write_sc && i < sc_rows) sc_base[i * sc_stride] = dv;
+      } else {
+        o[u] = scaled_int_to_float(Y, ex);
+        if (write_sc && i < sc_rows) sc_base[i * sc_stride] = scaled_int_to_double(Y, ex);
+      }
+      if (write_fin && !vec) fin_base[i * fin_stride] = o[u];
     }
-    const int ex = rowexp[c] + etau - 14 - 8 * (LEV - 1);
-    const long long i = i0 + c;
-    if (write_fin) {
-      if constexpr (sizeof(TO) == 8) fin_base[i * fin_stride] = scaled_int_to_double(Y, ex);
-      else fin_base[i * fin_stride] = scaled_int_to_float(Y, ex);
+    if (write_fin && vec) {
+      if constexpr (sizeof(TO) == 8)
+        *reinterpret_cast<double2 *>(fin_base + i0 + c0) = make_double2(o[0], o[1]);
+      else
+        *reinterpret_cast<float4 *>(fin_base + i0 + c0) = make_float4(o[0], o[1], o[2], o[3]);
     }
-    if (write_sc && i < sc_rows) sc_base[i * sc_stride] = scaled_int_to_double(Y, ex);
   }
 }
 
@@ -444,14 +465,20 @@ template <typename TI, typename TO, int KP, int S, int L>
 __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int A_BYTES = S * kTile * KP * 2;
-  constexpr int PITCH = KP + 1;  // staging row pitch (elements), odd to spread banks
+  // Staging row pitch (elements): odd for the y/z axes (one element per thread and copy,
+  // spread over the banks); for the x axis, where a pencil is a contiguous row copied in
+  // 16-byte chunks, a pitch whose rows stay 16-byte aligned.
+  constexpr int VE = 16 / sizeof(TI);  // elements per 16-byte chunk
+  constexpr int PITCH_MAX = KP + VE;
+  const bool xrow = P.xrow != 0;
+  const int pitch = xrow ? KP + VE : KP + 1;
   constexpr int NCH = KP / 8;    // 8-value K chunks per pencil
   const int R = P.rows;
   const int B_PASS_BYTES = S * R * KP * 2;
   uint16_t *sA = reinterpret_cast<uint16_t *>(smem);  // [2][S][128][KP]
   uint16_t *sB = reinterpret_cast<uint16_t *>(smem + 2 * A_BYTES);
   TI *stg = reinterpret_cast<TI *>(smem + 2 * A_BYTES + 2 * B_PASS_BYTES);
-  int *s_rowexp = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg) + kTile * PITCH * sizeof(TI));
+  int *s_rowexp = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg) + kTile * PITCH_MAX * sizeof(TI));
   int *s_emax = s_rowexp + 2 * 48;   // [2][128]
   // Pencil scales of the last 8 tiles: producers run at most 5 tiles ahead of
   // the epilogue (two A buffers, three TMEM pass buffers), so a slot and its
@@ -507,17 +534,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   if (warp < 8) {
     // ================================================================ producers (+ MMA issue by thread 0)
     const int pl = (warp & 3) * 32 + lane, half = warp >> 2;
+    const float inv_n2 = 1.0f / (float)P.n2;
+    const int cpr = E / VE;  // 16-byte chunks per pencil row (x axis); E * sizeof(TI) is a multiple of 16
+    const float inv_cpr = 1.0f / (float)cpr;
     auto prefetch = [&](int tile) {
       const int pp = tid & (kTile - 1), jq = tid >> 7;  // 2 threads per pencil
       const TileCoord c = tile_coord(P, tile, pp);
+      if (xrow) {
+        // x axis: the tile's pencil rows, 16-byte chunks, consecutive threads on consecutive
+        // chunks (rows of consecutive pencils are adjacent in memory)
+        const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+        const int lb = job / P.nf, q = job - lb * P.nf, np = P.n1 * P.n2;
+        const long long jb = P.in_field ? (long long)P.nf * P.extpre[P.blocks[lb]] + (long long)q * E3
+                                        : ((long long)lb * P.nf + q) * (long long)P.in_box;
+        const TI *in = static_cast<const TI *>(P.in) + jb;
+        for (int ch = tid; ch < kTile * cpr; ch += kProducers) {
+          // exact: the fractional parts stay >= 0.5 / divisor away from an integer
+          const int cp = __float2int_rz(((float)ch + 0.5f) * inv_cpr), r = ch - cp * cpr;
+          const int p = tj * kTile + cp;
+          if (p < np) {
+            const int t1 = __float2int_rz(((float)p + 0.5f) * inv_n2), t2 = p - t1 * P.n2;
+            const TI *src = in + (long long)(in_s1 + t1) * s_t1 + (long long)(in_s2 + t2) * s_t2 + r * VE;
+            cp_async16(stg + cp * pitch + r * VE, src);
+          }
+        }
+      }
       if (c.valid) {
-        long long ib = P.in_field ? (long long)P.nf * P.extpre[c.b] + (long long)c.q * E3
-                                  : ((long long)c.lb * P.nf + c.q) * (long long)P.in_box;
-        ib += (long long)(in_s1 + c.t1) * s_t1 + (long long)(in_s2 + c.t2) * s_t2;
-        const TI *src = static_cast<const TI *>(P.in) + ib;
-        for (int j = jq; j < E; j += 2) {
-          if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * PITCH + j, src + (long long)j * s_ax);
-          else cp_async4(stg + pp * PITCH + j, src + (long long)j * s_ax);
+        if (!xrow) {
+          long long ib = P.in_field ? (long long)P.nf * P.extpre[c.b] + (long long)c.q * E3
+                                    : ((long long)c.lb * P.nf + c.q) * (long long)P.in_box;
+          ib += (long long)(in_s1 + c.t1) * s_t1 + (long long)(in_s2 + c.t2) * s_t2;
+          const TI *src = static_cast<const TI *>(P.in) + ib;
+          for (int j = jq; j < E; j += 2) {
+            if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * pitch + j, src + (long long)j * s_ax);
+            else cp_async4(stg + pp * pitch + j, src + (long long)j * s_ax);
+          }
         }
         if (P.halo_in) {
           // previous iterate of the neighbours at k^c: d_lo from the lower neighbour's row N-2,
@@ -528,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
                                (long long)(tile_pencil(P, tile, pp));
           for (int d = 0; d < 2; ++d) {
             const double hv = ((P.halo_deg_mask >> d) & 1) ? P.halo_in[hp * 4 + 2 * d + (jq ? 0 : 1)] : 0.0;
-            stg[pp * PITCH + E + 2 * d + jq] = TI(hv);
+            stg[pp * pitch + E + 2 * d + jq] = TI(hv);
           }
         }
       }
@@ -550,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int j = (half * (NCH / 2) + h) * 8 + k;
-          v[h][k] = (j < P.kext && c.valid) ? stg[pl * PITCH + j] : TI(0);
+          v[h][k] = (j < P.kext && c.valid) ? stg[pl * pitch + j] : TI(0);
           em = max(em, biased_exp(v[h][k]));
         }
       }
@@ -662,9 +713,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
         const int *rexp = s_rowexp + ps * 48 + r0;
         if (RH == 16)
-          epilogue_rows<16, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows);
+          epilogue_rows<16, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows, P.xvec != 0);
         else
-          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows);
+          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows, P.xvec != 0);
       }
     }
   }
@@ -826,7 +877,7 @@ int levels_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 4 : 1; }
 // one CTA (holding all 512 TMEM columns) occupies an SM.
 size_t dense_smem(int KP, int S, int rows, size_t elem) {
   const size_t need = 2 * (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2 +
-                      (size_t)kTile * (KP + 1) * elem + (2 * 48 + 2 * kTile + 8 * kTile) * 4 + 16 * 8 + 64;
+                      (size_t)kTile * (KP + 16 / elem) * elem + (2 * 48 + 2 * kTile + 8 * kTile) * 4 + 16 * 8 + 64;
   return std::max(need, (size_t)116 * 1024);
 }
 
@@ -917,6 +968,10 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
     base.halo_deg_mask = (B->s[0].present ? 1 : 0) | (B->s[1].present ? 2 : 0);
     auto run = [&](DenseParams P) -> cfd_status {
       const int np = P.n1 * P.n2;
+      const size_t ein = (P.in_field && B->dtype == CFD_F32) ? 4 : 8;
+      const size_t eout = B->dtype == CFD_F32 ? 4 : 8;
+      P.xrow = P.axis == 2 && (E * ein) % 16 == 0 && ((uintptr_t)P.in & 15) == 0;
+      P.xvec = P.axis == 2 && (N * eout) % 16 == 0 && ((uintptr_t)P.out & 15) == 0;
       P.tiles_per_job = (np + kTile - 1) / kTile;
       P.ntiles = P.tiles_per_job * P.nblk * P.nf;
       const unsigned grid = (unsigned)std::min(P.ntiles, sms);
