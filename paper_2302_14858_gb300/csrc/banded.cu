@@ -21,25 +21,48 @@ __device__ __forceinline__ double ldg_d(const T *p) { return static_cast<double>
 
 // ---------------------------------------------------------------- ghost exchange
 
+// One thread per ghost cell, enumerated without idle threads: part A covers the
+// rows (fixed z, y) that lie in the ghost shell along y or z (all E values of x),
+// part B the x ghosts of the N^2 interior rows.  Consecutive threads take
+// consecutive x, so destination rows and source segments are contiguous.
 template <typename T>
 __global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N, int g,
                            const long long *__restrict__ extpre, const int *__restrict__ nbr) {
-  const int E = N + 2 * g;
-  const long long cells = (long long)E * E * E;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= cells) return;
+  const int E = N + 2 * g, G2 = 2 * g;
+  const int nA = (E * E - N * N) * E, nB = N * N * G2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nA + nB) return;
+  int x, y, z;
+  if (idx < nA) {
+    const int r = idx / E;
+    x = idx - r * E;
+    if (r < G2 * E) {              // z in the ghost shell: whole planes
+      const int zz = r / E;
+      y = r - zz * E;
+      z = zz < g ? zz : zz + N;
+    } else {                       // z interior, y in the ghost shell
+      const int r2 = r - G2 * E, zz = r2 / G2, yy = r2 - zz * G2;
+      z = g + zz;
+      y = yy < g ? yy : yy + N;
+    }
+  } else {                         // interior row, x ghosts
+    const int r = idx - nA, row = r / G2, xx = r - row * G2, zz = row / N;
+    x = xx < g ? xx : xx + N;
+    y = g + row - zz * N;
+    z = g + zz;
+  }
   const int job = blockIdx.y;
   const int lb = job / nf, q = job - lb * nf;
   const int b = blocks[lb];
-  const int x = (int)(idx % E), y = (int)((idx / E) % E), z = (int)(idx / ((long long)E * E));
   const int dx = x < g ? -1 : (x >= N + g ? 1 : 0);
   const int dy = y < g ? -1 : (y >= N + g ? 1 : 0);
   const int dz = z < g ? -1 : (z >= N + g ? 1 : 0);
-  if ((dx | dy | dz) == 0) return;
   const int nb = nbr[b * 26 + dir_index(dz, dy, dx)];
   if (nb < 0) return;
-  const long long src = ((long long)(z - dz * N) * E + (y - dy * N)) * E + (x - dx * N);
-  f[nf * extpre[b] + q * cells + idx] = f[nf * extpre[nb] + q * cells + src];
+  const long long cells = (long long)E * E * E;
+  const int dst = (z * E + y) * E + x;
+  const int src = ((z - dz * N) * E + (y - dy * N)) * E + (x - dx * N);
+  f[nf * extpre[b] + q * cells + dst] = f[nf * extpre[nb] + q * cells + src];
 }
 
 // ---------------------------------------------------------------- pencil solves
@@ -235,8 +258,8 @@ cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nf, cudaStream_t s
     const int N = B->sizes[gi];
     const int nblk = (int)B->groups[gi].size();
     const long long E = N + 2 * B->ng;
-    const long long cells = E * E * E;
-    dim3 grid((unsigned)((cells + 255) / 256), nblk * nf);
+    const long long ghosts = E * E * E - (long long)N * N * N;
+    dim3 grid((unsigned)((ghosts + 255) / 256), nblk * nf);
     launch_begin(KF_EXCHANGE, st);
     if (B->dtype == CFD_F64)
       k_exchange<double><<<grid, 256, 0, st>>>(static_cast<double *>(fields), nf, B->d_groups[gi], N, B->ng,

@@ -279,21 +279,22 @@ __device__ __forceinline__ long long fixed_of(float v, int emax) {
   return (u >> 31) ? -U : U;
 }
 
-// Balanced base-256 digits d_0..d_4 (|d| <= 128, d_0 most significant) of a
-// two's-complement F with |F| <= 2^39; returns the leading S as FP32 bit patterns.
+// Balanced base-256 digits d_0..d_4 (d_1..d_4 in [-128, 127], |d_0| <= 128, d_0 most
+// significant) of a two's-complement F with |F| <= 2^39; returns the leading S as FP32
+// bit patterns.  Adding 128 to each of the four low digit positions absorbs the carries:
+// the low word of V = F + 0x80808080 holds the bytes d_t + 128 and V >> 32 is d_0.  A
+// byte is turned into a float by placing it under the exponent of 2^23 (1 PRMT) and
+// subtracting 2^23 + 128 (exact).
 template <int S>
 __device__ __forceinline__ void digits_of(long long F, uint32_t (&out)[S]) {
-  const uint32_t lo = (uint32_t)F;
-  const int hi = (int)(F >> 32);
-  int d[5];
-  int c, x;
-  x = (int)(lo & 0xFF);         c = x >= 128; d[4] = x - (c << 8);
-  x = (int)((lo >> 8) & 0xFF) + c;  c = x >= 128; d[3] = x - (c << 8);
-  x = (int)((lo >> 16) & 0xFF) + c; c = x >= 128; d[2] = x - (c << 8);
-  x = (int)(lo >> 24) + c;          c = x >= 128; d[1] = x - (c << 8);
-  d[0] = hi + c;
+  const long long V = F + 0x80808080ll;
+  const uint32_t lo = (uint32_t)V;
+  out[0] = small_int_f32bits((int)(V >> 32));
 #pragma unroll
-  for (int t = 0; t < S; ++t) out[t] = small_int_f32bits(d[t]);
+  for (int t = 1; t < S; ++t) {
+    const uint32_t sel = 0x5440u | (uint32_t)(4 - t);  // byte 4-t of lo, then 0x00 0x00 0x4B
+    out[t] = __float_as_uint(__uint_as_float(__byte_perm(lo, 0x4B00u, sel)) - 8388736.0f);
+  }
 }
 
 __device__ __forceinline__ int biased_exp(double v) {
@@ -376,6 +377,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
   // the pass buffer can be reused as soon as every epilogue thread has its values
   asm volatile("tcgen05.fence::before_thread_sync;");
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t_empty_addr));
+  if (!write_fin && !write_sc) return;  // a pencil outside the outputs of this pass
   // 16-byte vector stores where the output axis is contiguous (x): pencil rows are
   // 16-byte aligned (N and the output offsets are multiples of 16 elements)
   constexpr int V = 16 / sizeof(TO);
