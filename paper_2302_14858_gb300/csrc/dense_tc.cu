@@ -237,16 +237,15 @@ __device__ __forceinline__ int acc_to_int(uint32_t bits) {
   return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
 }
 
-// Y * 2^E as an IEEE double, truncated to 53 bits (error below one unit in
-// the last place), built with integer instructions only.
+// Y * 2^E as an IEEE double, rounded to nearest.  The 64-bit conversion runs on
+// the FP64 pipe (otherwise idle in this kernel); the power-of-two scale is an add
+// to the exponent field.  A result below the normal range flushes to a signed zero
+// (|Y| < 2^55 and finite inputs keep it below the overflow range).
 __device__ __forceinline__ double scaled_int_to_double(long long Y, int E) {
-  const unsigned long long sgn = (unsigned long long)Y & (1ull << 63);
-  unsigned long long U = Y < 0 ? (unsigned long long)(-Y) : (unsigned long long)Y;
-  const int lz = __clzll((long long)U);
-  U <<= (lz & 63);
-  const int be = 63 - lz + E + 1023;
-  const unsigned long long bits = sgn | ((unsigned long long)be << 52) | ((U >> 11) & ((1ull << 52) - 1));
-  return (U == 0 || be <= 0) ? __longlong_as_double((long long)sgn) : __longlong_as_double((long long)bits);
+  const double d = __ll2double_rn(Y);
+  const int hi = __double2hiint(d), lo = __double2loint(d);
+  const int fe = (hi >> 20) & 0x7FF;  // 0 only for Y = 0
+  return (fe == 0 || fe + E <= 0) ? __hiloint2double(hi & (int)0x80000000, 0) : __hiloint2double(hi + (E << 20), lo);
 }
 
 __device__ __forceinline__ float scaled_int_to_float(long long Y, int E) {
@@ -257,14 +256,15 @@ __device__ __forceinline__ float scaled_int_to_float(long long Y, int E) {
 }
 
 // Signed fixed-point value F = round(v / tau * 2^39), |F| <= 2^39, of one input
-// element; tau = 2^(emax - bias + 1) is the pencil's power-of-two scale.
+// element; tau = 2^(emax - bias + 1) is the pencil's power-of-two scale (emax the
+// largest biased exponent of the pencil).  v * 2^(1061 - emax) is formed by an add
+// to the exponent field (it stays a normal number for e >= emax - 60; anything
+// smaller rounds to zero) and converted on the FP64 pipe.
 __device__ __forceinline__ long long fixed_of(double v, int emax) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((u >> 52) & 0x7FF);
-  const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);
-  const int sh = emax + 14 - e;  // >= 14
-  const long long U = (e == 0 || sh > 60) ? 0ll : (long long)(((m >> (sh - 1)) + 1ull) >> 1);
-  return (u >> 63) ? -U : U;
+  const int hi = __double2hiint(v), lo = __double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  const double w = __hiloint2double(hi + ((1061 - emax) << 20), lo);
+  return (e == 0 || e + 60 < emax) ? 0ll : __double2ll_rn(w);
 }
 
 __device__ __forceinline__ long long fixed_of(float v, int emax) {
@@ -621,6 +621,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       for (int h = 0; h < NCH / 2; ++h) {
         const int ch = half * (NCH / 2) + h;
         uint32_t w[S][4];
+        if (ch * 8 >= P.kext) {  // K padding: zero digits (warp-uniform branch)
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            uint4 *dst = reinterpret_cast<uint4 *>(Ab + (size_t)t * kTile * KP + ((size_t)row_group * NCH + ch) * 64 +
+                                                   row_in * 8);
+            *dst = make_uint4(0u, 0u, 0u, 0u);
+          }
+          continue;
+        }
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
           uint32_t d0[S], d1[S];
