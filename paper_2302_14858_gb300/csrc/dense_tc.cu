@@ -761,6 +761,43 @@ cfd_status launch_types(const DenseParams &P, int KP, int S, int L, size_t smem,
   }
 }
 
+// Ghost columns of an FP64 intermediate G = D_j f (box [N][d1][E], x fastest) copied
+// from the face neighbours' interior values: part A the x ghosts of the N rows
+// y = ylo..ylo+N-1, part B (do_y) the y ghosts of the interior x columns.  On a
+// same-size neighbour the copied value is the one local evaluation on the ghost
+// rows would produce (identical input data and arithmetic).
+__global__ void k_scratch_halo(double *G, const int *__restrict__ blocks, const int *__restrict__ lidx,
+                               const int *__restrict__ nbr, int nf, int N, int g, int d1, int ylo, int do_y,
+                               unsigned long long box) {
+  const int E = N + 2 * g, G2 = 2 * g;
+  const int nA = N * N * G2, nB = do_y ? N * G2 * N : 0;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nA + nB) return;
+  const int job = blockIdx.y, lb = job / nf, q = job - lb * nf;
+  const int b = blocks[lb];
+  int z, y, x, dy = 0, dx = 0;
+  if (idx < nA) {
+    const int r = idx / G2, xx = idx - r * G2;
+    z = r / N;
+    y = ylo + (r - z * N);
+    x = xx < g ? xx : xx + N;
+    dx = xx < g ? -1 : 1;
+  } else {
+    const int r = idx - nA, row = r / N;
+    x = g + (r - row * N);
+    z = row / G2;
+    const int yy = row - z * G2;
+    y = yy < g ? yy : yy + N;
+    dy = yy < g ? -1 : 1;
+  }
+  const int nb = nbr[b * 26 + dir_index_dev(0, dy, dx)];
+  if (nb < 0) return;
+  const int ln = lidx[nb];
+  const long long dst = ((long long)lb * nf + q) * (long long)box + ((long long)z * d1 + y) * E + x;
+  const long long src = ((long long)ln * nf + q) * (long long)box + ((long long)z * d1 + (y - dy * N)) * E + (x - dx * N);
+  G[dst] = G[src];
+}
+
 // ------------------------------------------------------------------ host planning
 
 struct DenseOp {        // one (group, axis, degree) operator
@@ -777,10 +814,12 @@ struct DenseGroup {
   DenseOp opI[3][2];     // iterated operator [D1 | c- | c+] with halo columns, dx-scaled
   DenseOp halo0[3];      // rows 1 and N-2 of [0]D per degree (16 rows), unscaled
   DenseOp haloI[3];      // rows 1 and N-2 of the iterated operator (16 rows), unscaled
+  bool faces_x = false, faces_y = false;  // every block has both x (y) face neighbours
 };
 
 struct DenseState {
   std::vector<DenseGroup> groups;
+  int *d_lidx = nullptr;  // device: block id -> index within its size group
 };
 
 DenseState *state_of(cfd_blocks_s *B) { return reinterpret_cast<DenseState *>(B->dense_state); }
@@ -873,9 +912,24 @@ cfd_status dense_bind(cfd_blocks_s *B) {
         if (s != CFD_OK) return s;
       }
     }
+    {
+      auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
+      G.faces_x = G.faces_y = true;
+      for (int b : B->groups[gi]) {
+        if (B->nbr[b * 26 + di(0, 0, -1)] < 0 || B->nbr[b * 26 + di(0, 0, 1)] < 0) G.faces_x = false;
+        if (B->nbr[b * 26 + di(0, -1, 0)] < 0 || B->nbr[b * 26 + di(0, 1, 0)] < 0) G.faces_y = false;
+      }
+    }
     st->groups.push_back(G);
   }
-  return CFD_OK;
+  std::vector<int> lidx(B->nblocks, 0);
+  for (size_t gi = 0; gi < B->groups.size(); ++gi)
+    for (size_t k = 0; k < B->groups[gi].size(); ++k) lidx[B->groups[gi][k]] = (int)k;
+  cfd_status s = cuda_fail(cudaMalloc((void **)&st->d_lidx, lidx.size() * 4), "cudaMalloc");
+  if (st->d_lidx) B->d_dense_ptrs.push_back(st->d_lidx);
+  if (s == CFD_OK)
+    s = cuda_fail(cudaMemcpy(st->d_lidx, lidx.data(), lidx.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  return s;
 }
 
 namespace {
@@ -1075,32 +1129,47 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       if ((s = run_stage(P, 2)) != CFD_OK) return s;
     }
     // S_y: D_y on (z interior, x extended if d_xy) -> d_y, d_yy, and G_y = D_y f for d_xy
+    // With face neighbours along x (and y), the intermediates are computed on the
+    // interior pencils only and their ghost columns copied from the neighbours.
+    auto scratch_halo = [&](double *Gs, int d1, int ylo, int do_y, unsigned long long box) -> cfd_status {
+      const int n = N * N * 2 * g * (do_y ? 2 : 1);
+      dim3 grid((unsigned)((n + 255) / 256), (unsigned)(base.nblk * nf));
+      launch_begin(KF_HALO, st);
+      k_scratch_halo<<<grid, 256, 0, st>>>(Gs, base.blocks, ds->d_lidx, B->d_nbr, nf, N, g, d1, ylo, do_y, box);
+      launch_end(KF_HALO, st);
+      return cuda_fail(cudaGetLastError(), "k_scratch_halo launch");
+    };
     if (ody >= 0 || odyy >= 0 || odxy >= 0) {
       const bool ext = odxy >= 0;
-      DenseParams P = field_stage(1, 0, 2, g, N, ext ? 0 : g, ext ? E : N);
+      const bool copy = ext && G.faces_x;  // interior pencils + ghost-column copy
+      DenseParams P = field_stage(1, 0, 2, g, N, (ext && !copy) ? 0 : g, (ext && !copy) ? E : N);
       const int m1 = (ody >= 0 && ext) ? 3 : (ody >= 0 ? 0 : (ext ? 2 : -1));
       set_segments(P, 1, m1, ody, odyy >= 0 ? 0 : -1, odyy);
       if (ext) {
         P.scratch_out = gy;
         P.sc_box = (unsigned long long)N * N * E;
         P.sc_dims[0] = N; P.sc_dims[1] = N; P.sc_dims[2] = E;
-        P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = 0;
+        P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = copy ? g : 0;
       }
       if ((s = run_stage(P, 1)) != CFD_OK) return s;
+      if (copy && (s = scratch_halo(gy, N, 0, 0, P.sc_box)) != CFD_OK) return s;
     }
     // S_z: D_z on (y, x) extended for d_xz / d_yz -> d_z, d_zz, and G_z = D_z f
     if (odz >= 0 || odzz >= 0 || odxz >= 0 || odyz >= 0) {
       const bool ext = odxz >= 0 || odyz >= 0;
-      DenseParams P = field_stage(0, 1, 2, ext ? 0 : g, ext ? E : N, ext ? 0 : g, ext ? E : N);
+      const bool copy = ext && G.faces_x && G.faces_y;
+      const bool wide = ext && !copy;
+      DenseParams P = field_stage(0, 1, 2, wide ? 0 : g, wide ? E : N, wide ? 0 : g, wide ? E : N);
       const int m1 = (odz >= 0 && ext) ? 3 : (odz >= 0 ? 0 : (ext ? 2 : -1));
       set_segments(P, 0, m1, odz, odzz >= 0 ? 0 : -1, odzz);
       if (ext) {
         P.scratch_out = gz;
         P.sc_box = (unsigned long long)N * E * E;
         P.sc_dims[0] = N; P.sc_dims[1] = E; P.sc_dims[2] = E;
-        P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = 0;
+        P.sc_start[0] = 0; P.sc_start[1] = copy ? g : 0; P.sc_start[2] = copy ? g : 0;
       }
       if ((s = run_stage(P, 0)) != CFD_OK) return s;
+      if (copy && (s = scratch_halo(gz, E, g, 1, P.sc_box)) != CFD_OK) return s;
     }
     // T stages on the intermediates (one order of the mixed product: the closed
     // block operators of two axes commute, D_i D_j = D_j D_i)
