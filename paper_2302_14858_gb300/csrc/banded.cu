@@ -5,6 +5,8 @@
 // sum_m c_m f_{k+m} over m = -M..M (or the closure's -h..h) in increasing m,
 // then scaled by dx^{-d}; the solve uses the precomputed Thomas factors of the
 // block system (identical for every pencil of a block size).
+#include <type_traits>
+
 #include "cfd_internal.h"
 
 namespace cfd {
@@ -24,10 +26,13 @@ __device__ __forceinline__ double ldg_d(const T *p) { return static_cast<double>
 // One thread per ghost cell, enumerated without idle threads: part A covers the
 // rows (fixed z, y) that lie in the ghost shell along y or z (all E values of x),
 // part B the x ghosts of the N^2 interior rows.  Consecutive threads take
-// consecutive x, so destination rows and source segments are contiguous.
-template <typename T>
-__global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N, int g,
+// consecutive x, so destination rows and source segments are contiguous.  The
+// common (N, g) pairs are compiled with constant sizes (divisions become
+// multiply-shifts); NC = 0 takes them at run time.
+template <typename T, int NC, int GC>
+__global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N_, int g_,
                            const long long *__restrict__ extpre, const int *__restrict__ nbr) {
+  const int N = NC ? NC : N_, g = NC ? GC : g_;
   const int E = N + 2 * g, G2 = 2 * g;
   const int nA = (E * E - N * N) * E, nB = N * N * G2;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,10 +64,10 @@ __global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N, 
   const int dz = z < g ? -1 : (z >= N + g ? 1 : 0);
   const int nb = nbr[b * 26 + dir_index(dz, dy, dx)];
   if (nb < 0) return;
-  const long long cells = (long long)E * E * E;
+  const int cells = E * E * E;
   const int dst = (z * E + y) * E + x;
-  const int src = ((z - dz * N) * E + (y - dy * N)) * E + (x - dx * N);
-  f[nf * extpre[b] + q * cells + dst] = f[nf * extpre[nb] + q * cells + src];
+  const int src = dst - ((dz * E + dy) * E + dx) * N;
+  f[nf * extpre[b] + (long long)(q * cells + dst)] = f[nf * extpre[nb] + (long long)(q * cells + src)];
 }
 
 // ---------------------------------------------------------------- pencil solves
@@ -261,12 +266,23 @@ cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nf, cudaStream_t s
     const long long ghosts = E * E * E - (long long)N * N * N;
     dim3 grid((unsigned)((ghosts + 255) / 256), nblk * nf);
     launch_begin(KF_EXCHANGE, st);
-    if (B->dtype == CFD_F64)
-      k_exchange<double><<<grid, 256, 0, st>>>(static_cast<double *>(fields), nf, B->d_groups[gi], N, B->ng,
-                                               B->d_extpre, B->d_nbr);
-    else
-      k_exchange<float><<<grid, 256, 0, st>>>(static_cast<float *>(fields), nf, B->d_groups[gi], N, B->ng,
-                                              B->d_extpre, B->d_nbr);
+    const int g = B->ng;
+    auto go = [&](auto tag, auto nc, auto gc) {
+      using T = decltype(tag);
+      k_exchange<T, decltype(nc)::value, decltype(gc)::value><<<grid, 256, 0, st>>>(
+          static_cast<T *>(fields), nf, B->d_groups[gi], N, g, B->d_extpre, B->d_nbr);
+    };
+    auto by_size = [&](auto tag) {
+      using I = std::integral_constant<int, 0>;
+      if (g == 4 && N == 16) go(tag, std::integral_constant<int, 16>(), std::integral_constant<int, 4>());
+      else if (g == 4 && N == 32) go(tag, std::integral_constant<int, 32>(), std::integral_constant<int, 4>());
+      else if (g == 4 && N == 8) go(tag, std::integral_constant<int, 8>(), std::integral_constant<int, 4>());
+      else if (g == 5 && N == 16) go(tag, std::integral_constant<int, 16>(), std::integral_constant<int, 5>());
+      else if (g == 5 && N == 32) go(tag, std::integral_constant<int, 32>(), std::integral_constant<int, 5>());
+      else go(tag, I(), I());
+    };
+    if (B->dtype == CFD_F64) by_size(double());
+    else by_size(float());
     launch_end(KF_EXCHANGE, st);
     cfd_status s = cuda_fail(cudaGetLastError(), "k_exchange launch");
     if (s != CFD_OK) return s;

@@ -766,9 +766,11 @@ cfd_status launch_types(const DenseParams &P, int KP, int S, int L, size_t smem,
 // y = ylo..ylo+N-1, part B (do_y) the y ghosts of the interior x columns.  On a
 // same-size neighbour the copied value is the one local evaluation on the ghost
 // rows would produce (identical input data and arithmetic).
+template <int NC, int GC>
 __global__ void k_scratch_halo(double *G, const int *__restrict__ blocks, const int *__restrict__ lidx,
-                               const int *__restrict__ nbr, int nf, int N, int g, int d1, int ylo, int do_y,
+                               const int *__restrict__ nbr, int nf, int N_, int g_, int d1, int ylo, int do_y,
                                unsigned long long box) {
+  const int N = NC ? NC : N_, g = NC ? GC : g_;  // constant sizes turn the divisions into multiply-shifts
   const int E = N + 2 * g, G2 = 2 * g;
   const int nA = N * N * G2, nB = do_y ? N * G2 * N : 0;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1135,7 +1137,12 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       const int n = N * N * 2 * g * (do_y ? 2 : 1);
       dim3 grid((unsigned)((n + 255) / 256), (unsigned)(base.nblk * nf));
       launch_begin(KF_HALO, st);
-      k_scratch_halo<<<grid, 256, 0, st>>>(Gs, base.blocks, ds->d_lidx, B->d_nbr, nf, N, g, d1, ylo, do_y, box);
+      auto kern = k_scratch_halo<0, 0>;
+      if (N == 32 && g == 4) kern = k_scratch_halo<32, 4>;
+      else if (N == 16 && g == 4) kern = k_scratch_halo<16, 4>;
+      else if (N == 32 && g == 5) kern = k_scratch_halo<32, 5>;
+      else if (N == 16 && g == 5) kern = k_scratch_halo<16, 5>;
+      kern<<<grid, 256, 0, st>>>(Gs, base.blocks, ds->d_lidx, B->d_nbr, nf, N, g, d1, ylo, do_y, box);
       launch_end(KF_HALO, st);
       return cuda_fail(cudaGetLastError(), "k_scratch_halo launch");
     };
