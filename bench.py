@@ -47,6 +47,8 @@ WORKLOADS = {
     "cfd128_b32_f4_fp64": dict(kind="uniform", NM=128, N=32, nf=4, fields=3, dtype="f64", n_iter=0),
     # 448 blocks 16^3 + 64 blocks 32^3, 22 FP32 fields, 9 ops, closures only
     "box448x16_64x32_f22_fp32": dict(kind="boxinbox", nf=22, fields=4, dtype="f32", n_iter=0),
+    # linear wave u_tt = Laplacian u, 256^3 as 512 blocks of 32^3, plane waves |k| <= 20, RK4, dt = 0.25 dx
+    "wave256_b32_rk4": dict(kind="wave", NM=256, N=32, nf=2, dtype="f64", n_iter=0, modes=8, kmax=20.0),
 }
 DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 
@@ -229,6 +231,25 @@ def cpu_baseline(spec, seconds=12.0):
     s1 = C.Sch(1, e1["a"], tuple(e1["rhs"]), tuple(e1["closure"]))
     s2 = C.Sch(2, e2["a"], tuple(e2["rhs"]), tuple(e2["closure"]))
     g = 4
+    if spec["kind"] == "wave":
+        # sample: one RK4 step of the oracle on 64^3 as 8 blocks of 32^3 (units: 3 ops x points x 4 stages)
+        NS, N = 64, spec["N"]
+        pw = W.plane_waves(2302 + 5, spec["modes"], spec["kmax"])
+        dx = 2 * np.pi / NS
+        x = (np.arange(NS) + 0.5) * dx
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        p, k = pw.phi_at(0.0, X, Y, Z), pw.K_at(0.0, X, Y, Z)
+        units, reps = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            p, k = C.wave_rk4_step(p, k, 0.25 * dx, s2, (dx, dx, dx), N, g, spec["n_iter"])
+            units += 3 * NS ** 3 * 4
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        el = time.perf_counter() - t0
+        return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle wave_rk4_step, {NS}^3 as {(NS // N) ** 3} blocks of {N}^3, {reps} RK4 steps"}
     if spec["kind"] == "uniform":
         NM, N = spec["NM"], spec["N"]
         # sample: one field on a (NM/2)^3 periodic sub-problem with the same block size
@@ -347,6 +368,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, spec, rank)
+    if spec["kind"] == "wave":
+        return run_wave(args, spec)
 
     import torch
     if world > 1:
@@ -504,6 +527,123 @@ def main():
                        "input_bytes": in_bytes, "parallelism": f"replicas x{world}"},
             "roofline": roof, "compare": compare, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_wave(args, spec):
+    """The RK4 wave driver: Gpoint-ops/s (3 second-derivative ops x points x 4 stages per step),
+    steps/s, and the phase and amplitude errors of every plane-wave mode against the exact
+    solution after the timed steps (both the requested path and the FP64 banded path)."""
+    import torch
+    from paper_2302_14858_gb300 import cfd, workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    NM, N, g = spec["NM"], spec["N"], 4
+    mesh = W.uniform_mesh(NM, N, g)
+    nb, E = NM // N, N + 2 * g
+    dx = 2 * math.pi / NM
+    dt = 0.25 * dx
+    pw = W.plane_waves(2302 + 5, spec["modes"], spec["kmax"])
+    x = (torch.arange(NM, dtype=torch.float64, device=dev) + 0.5) * dx
+    idx = (torch.arange(nb, device=dev)[:, None] * N + torch.arange(-g, N + g, device=dev)[None, :]) % NM
+
+    def layout(fg):
+        ext = fg[idx[:, None, None, :, None, None], idx[None, :, None, None, :, None], idx[None, None, :, None, None, :]]
+        return ext.reshape(-1).contiguous()
+
+    def plane(t, deriv):
+        Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+        out = torch.zeros_like(X)
+        for kv, A, p in zip(pw.k, pw.A, pw.phi):
+            w = float(np.sqrt((kv ** 2).sum()))
+            arg = float(kv[0]) * X + float(kv[1]) * Y + float(kv[2]) * Z - w * t + float(p)
+            out += float(A) * (w * torch.sin(arg) if deriv else torch.cos(arg))
+        return out
+
+    phi0, K0 = layout(plane(0.0, False)), layout(plane(0.0, True))
+    d1, d2 = scheme_descs()
+    blocks = cfd.cfd_blocks_bind(cfd.cfd_scheme_create(d1, d2), mesh.n, mesh.dx, mesh.neighbors, g, cfd.CFD_F64)
+    stream = torch.cuda.current_stream(dev)
+    phi, K = phi0.clone(), K0.clone()
+
+    def run(prec, steps, timed_region):
+        ws = cfd.cfd_wave_workspace(blocks, prec, spec["n_iter"])
+        work = torch.empty(ws, dtype=torch.uint8, device=dev)
+        phi.copy_(phi0)
+        K.copy_(K0)
+        for _ in range(args.warmup):
+            cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream)
+        phi.copy_(phi0)
+        K.copy_(K0)
+        torch.cuda.synchronize()
+        ms = timed(lambda: cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream),
+                   steps, stream, torch) if timed_region else None
+        if not timed_region:
+            for _ in range(steps):
+                cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream)
+            torch.cuda.synchronize()
+        cfd.cfd_sync_status(blocks, stream)
+        return ms, mode_errors(steps * dt)
+
+    def mode_errors(t):
+        # interior values back to the global grid, then project on every plane-wave mode
+        f = phi.view(nb, nb, nb, E, E, E)[:, :, :, g:g + N, g:g + N, g:g + N]
+        fg = f.permute(0, 3, 1, 4, 2, 5).reshape(NM, NM, NM)
+        Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+        amp, ph = 0.0, 0.0
+        for kv, A, p in zip(pw.k, pw.A, pw.phi):
+            w = float(np.sqrt((kv ** 2).sum()))
+            arg = float(kv[0]) * X + float(kv[1]) * Y + float(kv[2]) * Z
+            c = complex((fg * torch.cos(arg)).mean().item() * 2.0, -(fg * torch.sin(arg)).mean().item() * 2.0)
+            want = float(A) * complex(math.cos(float(p) - w * t), math.sin(float(p) - w * t))
+            r = c / want
+            amp = max(amp, abs(abs(r) - 1.0))
+            ph = max(ph, abs(math.atan2(r.imag, r.real)))
+        return {"amplitude_err_max": amp, "phase_err_max_rad": ph}
+
+    prec = PREC[args.prec]
+    clocks = ClockSampler(local)
+    launches0 = cfd.cfd_kernel_launches()
+    clocks.start()
+    time.sleep(0.3)
+    ms, err = run(prec, args.steps, True)
+    clk = clocks.stop()
+    launches = cfd.cfd_kernel_launches() - launches0
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    units = 3 * NM ** 3 * 4
+    cpu = cpu_baseline(spec) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    compare = None
+    if not args.no_compare and prec != PREC["fp64_banded"]:
+        ms64, err64 = run(PREC["fp64_banded"], args.steps, True)
+        compare = {"fp64_banded": {"value": round(units / (ms64 * 1e-3) / 1e9, 4), "ms_per_step": round(ms64, 4),
+                                   **err64},
+                   "speedup_vs_fp64_banded": round(ms64 / ms, 3)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(units * world / (ms * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded plane waves)",
+            "config": {"workload": args.workload, "path": args.prec, "n_iter": spec["n_iter"], "blocks": mesh.nblocks,
+                       "dt_over_dx": 0.25, "modes": spec["modes"], "kmax": spec["kmax"],
+                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+            "steps_per_s": round(1e3 / ms * world, 3), "t_final": args.steps * dt, **err,
+            "compare": compare, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line))
     if world > 1:

@@ -23,14 +23,16 @@ struct StageArgs {
   double c;             // 0.5 dt, 0.5 dt, dt, dt/6
 };
 
+// NC: the block size as a compile-time constant (0: taken from A.N at run time).
+template <int NC>
 __global__ void k_rk_combine(const StageArgs A) {
-  const int N = A.N, E = N + 2 * A.g;
-  const long long n3 = (long long)N * N * N;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = NC ? NC : A.N, E = N + 2 * A.g;
+  const int n3 = N * N * N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
   const int b = A.blocks[blockIdx.y];
-  const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((long long)N * N));
-  const long long e = A.extpre[b] + ((long long)(z + A.g) * E + (y + A.g)) * E + (x + A.g);
+  const int x = i % N, y = (i / N) % N, z = i / (N * N);
+  const long long e = A.extpre[b] + ((z + A.g) * E + (y + A.g)) * E + (x + A.g);
   const long long in = A.intpre[b] + i;
   const double *L = A.lap + 3 * A.intpre[b];
   const double lap = __dadd_rn(__dadd_rn(L[i], L[n3 + i]), L[2 * n3 + i]);
@@ -133,7 +135,10 @@ extern "C" cfd_status cfd_wave_rk_step(cfd_blocks_t B, void *phi, void *K, doubl
       const long long n3 = (long long)A.N * A.N * A.N;
       dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)B->groups[gi].size());
       launch_begin(KF_RK, st);
-      k_rk_combine<<<grid, 256, 0, st>>>(A);
+      if (A.N == 32) k_rk_combine<32><<<grid, 256, 0, st>>>(A);
+      else if (A.N == 16) k_rk_combine<16><<<grid, 256, 0, st>>>(A);
+      else if (A.N == 8) k_rk_combine<8><<<grid, 256, 0, st>>>(A);
+      else k_rk_combine<0><<<grid, 256, 0, st>>>(A);
       launch_end(KF_RK, st);
       if ((s = cuda_fail(cudaGetLastError(), "k_rk_combine launch")) != CFD_OK) return s;
     }

@@ -232,3 +232,39 @@ def test_exact_slices_fp32_uneven_blocks(lib, torch):
             worst = max(worst, err)
     print("fp32 exact-slice max rel err", worst)
     assert worst < TOL_EXACT32
+
+
+@pytest.mark.parametrize("n_iter", [0, 1])
+def test_wave_rk4_tensor_cores(lib, torch, n_iter):
+    """The RK4 wave driver with the tensor-core Laplacian vs the oracle's RK4 (3 steps, 64^3, 16^3 blocks)."""
+    NM, N, g = 64, 16, 4
+    pw = W.plane_waves(13, 4, 10.0)
+    dx = 2 * np.pi / NM
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi0, K0 = pw.phi_at(0.0, X, Y, Z), pw.K_at(0.0, X, Y, Z)
+    mesh = W.uniform_mesh(NM, N, g)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    E = N + 2 * g
+    pe = C.ghost_fill_3d(phi0, N, g).reshape(mesh.nblocks, E, E, E)
+    ke = C.ghost_fill_3d(K0, N, g).reshape(mesh.nblocks, E, E, E)
+    tp = torch.from_numpy(pe.reshape(-1).copy()).cuda()
+    tk = torch.from_numpy(ke.reshape(-1).copy()).cuda()
+    ws = lib.cfd_wave_workspace(B, lib.CFD_TC_BF16_EXACT, n_iter)
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    dt = 0.25 * dx
+    s2 = oracle_sch("Q13_1_d2")
+    p, k = phi0, K0
+    for _ in range(3):
+        lib.cfd_wave_rk_step(B, tp, tk, dt, lib.CFD_TC_BF16_EXACT, n_iter, work)
+        p, k = C.wave_rk4_step(p, k, dt, s2, (dx, dx, dx), N, g, n_iter)
+    lib.cfd_sync_status(B)
+    nb = NM // N
+    gp = tp.cpu().numpy().reshape(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
+    gk = tk.cpu().numpy().reshape(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
+    gp = C.blocks_to_global(gp.reshape(nb, nb, nb, N, N, N))
+    gk = C.blocks_to_global(gk.reshape(nb, nb, nb, N, N, N))
+    print("wave tc rel err", rel_max(gp, p), rel_max(gk, k))
+    assert rel_max(gp, p) < TOL_EXACT64
+    assert rel_max(gk, k) < TOL_EXACT64
