@@ -357,6 +357,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="also time the step replayed from a captured CUDA graph")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -489,6 +490,32 @@ def main():
                    "max_rel_err_per_op": {op: float(rel[:, i].max()) for i, op in enumerate(cfd.OPS)}}
         del ref
 
+    # the same step captured once into a CUDA graph and replayed (launch overhead removed)
+    graph = None
+    if args.graph:
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+
+        def step_cur():
+            cur = torch.cuda.current_stream(dev)
+            cfd.cfd_exchange_ghosts(blocks, fields, nf, cur)
+            cfd.cfd_apply(blocks, fields, nf, mask, prec, n_iter, out, work, cur)
+
+        with torch.cuda.stream(side):
+            step_cur()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            step_cur()
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        ms_g = timed(g.replay, args.steps, torch.cuda.current_stream(dev), torch)
+        cfd.cfd_sync_status(blocks, stream)
+        graph = {"value": round(units * world / (ms_g * 1e-3) / 1e9, 4), "ms_per_step": round(ms_g, 5),
+                 "launches_per_step": round(launches / args.steps, 2)}
+
     # end-to-end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -525,7 +552,7 @@ def main():
                        "blocks": mesh.nblocks, "points_per_field": nint,
                        "l2": "inputs larger than L2" if in_bytes > L2_BYTES else "inputs fit L2",
                        "input_bytes": in_bytes, "parallelism": f"replicas x{world}"},
-            "roofline": roof, "compare": compare, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "compare": compare, "cpu_baseline": cpu, "e2e": e2e, "graph": graph,
             "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line))

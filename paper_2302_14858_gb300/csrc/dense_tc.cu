@@ -743,9 +743,20 @@ cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned g
   if (S == 5 && L == 4) fn = k_dense<TI, TO, KP, 5, 4>;
   else if (S == 2 && L == 1) fn = k_dense<TI, TO, KP, 2, 1>;
   else { set_error("dense: unsupported slice configuration"); return CFD_ERR_UNSUPPORTED; }
-  cfd_status s = cuda_fail(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                           "cudaFuncSetAttribute");
+  // The shared-memory opt-in is set once per device and instantiation (and raised when a
+  // launch needs more), so that later calls issue nothing but the launch: a stream being
+  // captured into a CUDA graph sees only kernel nodes.
+  static size_t opted[2][64] = {};  // [slice configuration][device]
+  const int v = S == 5 ? 0 : 1;
+  int dev = 0;
+  cfd_status s = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
   if (s != CFD_OK) return s;
+  if (dev < 0 || dev >= 64 || opted[v][dev] < smem) {
+    s = cuda_fail(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "cudaFuncSetAttribute");
+    if (s != CFD_OK) return s;
+    if (dev >= 0 && dev < 64) opted[v][dev] = smem;
+  }
   launch_begin(KF_DENSE, st);
   fn<<<grid, kThreads, smem, st>>>(P);
   launch_end(KF_DENSE, st);

@@ -268,3 +268,39 @@ def test_wave_rk4_tensor_cores(lib, torch, n_iter):
     print("wave tc rel err", rel_max(gp, p), rel_max(gk, k))
     assert rel_max(gp, p) < TOL_EXACT64
     assert rel_max(gk, k) < TOL_EXACT64
+
+
+def test_cuda_graph_capture_replays_exchange_and_apply(lib, torch):
+    """Ghost exchange + tensor-core apply captured in a CUDA graph: replay equals the eager result."""
+    NM, N, g = 64, 16, 4
+    fs = fields4(404)
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    dev = torch.device("cuda", 0)
+    fields = torch.from_numpy(buf.copy()).to(dev)
+    nint = mesh.nblocks * N ** 3
+    out = torch.zeros(nint * 4 * 9, dtype=torch.float64, device=dev)
+    ws = lib.cfd_apply_workspace(B, 4, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 1)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+
+    def step():
+        lib.cfd_exchange_ghosts(B, fields, 4)
+        lib.cfd_apply(B, fields, 4, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 1, out, work)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()   # eager (also sets the kernels' shared-memory opt-in before capture)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager = out.clone()
+    out.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    lib.cfd_sync_status(B)
+    assert torch.equal(out, eager)
