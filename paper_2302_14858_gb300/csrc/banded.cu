@@ -23,24 +23,31 @@ __device__ __forceinline__ double ldg_d(const T *p) { return static_cast<double>
 
 // ---------------------------------------------------------------- ghost exchange
 
-// One thread per ghost cell, enumerated without idle threads: part A covers the
-// rows (fixed z, y) that lie in the ghost shell along y or z (all E values of x),
-// part B the x ghosts of the N^2 interior rows.  Consecutive threads take
-// consecutive x, so destination rows and source segments are contiguous.  The
-// common (N, g) pairs are compiled with constant sizes (divisions become
-// multiply-shifts); NC = 0 takes them at run time.
-template <typename T, int NC, int GC>
+template <typename T, int V> struct VecOf { using type = T; };
+template <> struct VecOf<double, 2> { using type = double2; };
+template <> struct VecOf<float, 4> { using type = float4; };
+
+// One thread per V consecutive ghost cells along x (V values = 16 bytes where the
+// ghost width, N and the rows keep 16-byte alignment; V = 1 otherwise), enumerated
+// without idle threads: part A covers the rows (fixed z, y) that lie in the ghost
+// shell along y or z (all of x), part B the x ghosts of the N^2 interior rows.
+// Consecutive threads take consecutive x, so destination rows and source segments
+// are contiguous.  The common (N, g) pairs are compiled with constant sizes
+// (divisions become multiply-shifts); NC = 0 takes them at run time.
+template <typename T, int NC, int GC, int V>
 __global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N_, int g_,
                            const long long *__restrict__ extpre, const int *__restrict__ nbr) {
+  using VT = typename VecOf<T, V>::type;
   const int N = NC ? NC : N_, g = NC ? GC : g_;
-  const int E = N + 2 * g, G2 = 2 * g;
-  const int nA = (E * E - N * N) * E, nB = N * N * G2;
+  const int E = N + 2 * g, Ev = E / V, gv = g / V, Nv = N / V, G2v = 2 * gv;
+  const int nA = (E * E - N * N) * Ev, nB = N * N * G2v;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nA + nB) return;
   int x, y, z;
   if (idx < nA) {
-    const int r = idx / E;
-    x = idx - r * E;
+    const int r = idx / Ev;
+    x = (idx - r * Ev) * V;
+    const int G2 = 2 * g;
     if (r < G2 * E) {              // z in the ghost shell: whole planes
       const int zz = r / E;
       y = r - zz * E;
@@ -51,8 +58,8 @@ __global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N_,
       y = yy < g ? yy : yy + N;
     }
   } else {                         // interior row, x ghosts
-    const int r = idx - nA, row = r / G2, xx = r - row * G2, zz = row / N;
-    x = xx < g ? xx : xx + N;
+    const int r = idx - nA, row = r / G2v, xx = r - row * G2v, zz = row / N;
+    x = (xx < gv ? xx : xx + Nv) * V;
     y = g + row - zz * N;
     z = g + zz;
   }
@@ -67,7 +74,8 @@ __global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N_,
   const int cells = E * E * E;
   const int dst = (z * E + y) * E + x;
   const int src = dst - ((dz * E + dy) * E + dx) * N;
-  f[nf * extpre[b] + (long long)(q * cells + dst)] = f[nf * extpre[nb] + (long long)(q * cells + src)];
+  *reinterpret_cast<VT *>(f + nf * extpre[b] + (long long)(q * cells + dst)) =
+      *reinterpret_cast<const VT *>(f + nf * extpre[nb] + (long long)(q * cells + src));
 }
 
 // ---------------------------------------------------------------- pencil solves
@@ -264,25 +272,31 @@ cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nf, cudaStream_t s
     const int nblk = (int)B->groups[gi].size();
     const long long E = N + 2 * B->ng;
     const long long ghosts = E * E * E - (long long)N * N * N;
-    dim3 grid((unsigned)((ghosts + 255) / 256), nblk * nf);
-    launch_begin(KF_EXCHANGE, st);
     const int g = B->ng;
-    auto go = [&](auto tag, auto nc, auto gc) {
+    launch_begin(KF_EXCHANGE, st);
+    auto go = [&](auto tag, auto nc, auto gc, auto vc) {
       using T = decltype(tag);
-      k_exchange<T, decltype(nc)::value, decltype(gc)::value><<<grid, 256, 0, st>>>(
+      constexpr int V = decltype(vc)::value;
+      dim3 grid((unsigned)((ghosts / V + 255) / 256), nblk * nf);
+      k_exchange<T, decltype(nc)::value, decltype(gc)::value, V><<<grid, 256, 0, st>>>(
           static_cast<T *>(fields), nf, B->d_groups[gi], N, g, B->d_extpre, B->d_nbr);
     };
-    auto by_size = [&](auto tag) {
+    auto by_size = [&](auto tag, auto vc) {
       using I = std::integral_constant<int, 0>;
-      if (g == 4 && N == 16) go(tag, std::integral_constant<int, 16>(), std::integral_constant<int, 4>());
-      else if (g == 4 && N == 32) go(tag, std::integral_constant<int, 32>(), std::integral_constant<int, 4>());
-      else if (g == 4 && N == 8) go(tag, std::integral_constant<int, 8>(), std::integral_constant<int, 4>());
-      else if (g == 5 && N == 16) go(tag, std::integral_constant<int, 16>(), std::integral_constant<int, 5>());
-      else if (g == 5 && N == 32) go(tag, std::integral_constant<int, 32>(), std::integral_constant<int, 5>());
-      else go(tag, I(), I());
+      if (g == 4 && N == 16) go(tag, std::integral_constant<int, 16>(), std::integral_constant<int, 4>(), vc);
+      else if (g == 4 && N == 32) go(tag, std::integral_constant<int, 32>(), std::integral_constant<int, 4>(), vc);
+      else if (g == 4 && N == 8) go(tag, std::integral_constant<int, 8>(), std::integral_constant<int, 4>(), vc);
+      else go(tag, I(), I(), vc);
     };
-    if (B->dtype == CFD_F64) by_size(double());
-    else by_size(float());
+    // 16-byte copies need g, N (hence E) multiples of the vector width and an aligned buffer
+    const bool al16 = ((uintptr_t)fields & 15) == 0;
+    if (B->dtype == CFD_F64) {
+      if (al16 && g % 2 == 0) by_size(double(), std::integral_constant<int, 2>());
+      else by_size(double(), std::integral_constant<int, 1>());
+    } else {
+      if (al16 && g % 4 == 0 && N % 4 == 0) by_size(float(), std::integral_constant<int, 4>());
+      else by_size(float(), std::integral_constant<int, 1>());
+    }
     launch_end(KF_EXCHANGE, st);
     cfd_status s = cuda_fail(cudaGetLastError(), "k_exchange launch");
     if (s != CFD_OK) return s;
