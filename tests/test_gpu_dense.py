@@ -304,3 +304,25 @@ def test_cuda_graph_capture_replays_exchange_and_apply(lib, torch):
     torch.cuda.synchronize()
     lib.cfd_sync_status(B)
     assert torch.equal(out, eager)
+
+
+@pytest.mark.parametrize("fam,n_iter", [("P1", 0), ("P2", 1), ("P3", 0), ("P3", 1)])
+def test_pade_family_both_paths(lib, torch, fam, n_iter):
+    """Padé P^1_{1,2,3} (4th, 6th, 8th order) with their closures P-bar_{3,4,5}: stencil widths
+    M = 1..3, closure half-widths 3..5 (8th order needs 5 ghost layers), on both GPU paths."""
+    NM, N = 64, 16
+    g = 5 if fam == "P3" else 4
+    r = W.rng(600 + int(fam[1]) + 10 * n_iter)
+    fs = [W.sine_sum(r, 8, 1, 12), W.gaussian(r, 0.1)]
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc(f"{fam}_d1"), desc(f"{fam}_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    s1, s2 = oracle_sch(f"{fam}_d1"), oracle_sch(f"{fam}_d2")
+    tc = apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, n_iter).reshape(mesh.nblocks, 2, 9, N, N, N)
+    fp = apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, lib.CFD_FP64_BANDED, n_iter).reshape(mesh.nblocks, 2, 9, N, N, N)
+    for q in range(2):
+        ref = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, n_iter)
+        for i, op in enumerate(OPS):
+            want = ref[op].reshape(mesh.nblocks, N, N, N)
+            assert rel_max(fp[:, q, i], want) < 1e-12, (fam, q, op)
+            assert rel_max(tc[:, q, i], want) < TOL_EXACT64, (fam, q, op)
