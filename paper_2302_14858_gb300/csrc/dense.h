@@ -35,6 +35,10 @@ struct DenseParams {
   int halo_deg_mask;         // degrees whose halo columns are filled (bit d-1)
   int xrow;                  // x-axis stage with 16-byte aligned pencil rows: chunked row copies
   int xvec;                  // x-axis stage with a 16-byte aligned output: vector stores
+  // Consecutive block ids (blocks[lb] = b0 + lb): offsets follow from the job index
+  // (no dependent table loads in the tile loop)
+  int contig, b0;
+  long long ext0, int0;      // extpre[b0], intpre[b0]
   int *status;
 };
 

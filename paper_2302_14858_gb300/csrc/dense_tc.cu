@@ -455,7 +455,7 @@ __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, 
   const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
   c.lb = job / P.nf;
   c.q = job - c.lb * P.nf;
-  c.b = P.blocks[c.lb];
+  c.b = P.contig ? P.b0 + c.lb : P.blocks[c.lb];
   const int p = tj * kTile + pencil;
   c.valid = p < P.n1 * P.n2;
   c.t1 = c.valid ? p / P.n2 : 0;
@@ -547,8 +547,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
         // chunks (rows of consecutive pencils are adjacent in memory)
         const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
         const int lb = job / P.nf, q = job - lb * P.nf, np = P.n1 * P.n2;
-        const long long jb = P.in_field ? (long long)P.nf * P.extpre[P.blocks[lb]] + (long long)q * E3
-                                        : ((long long)lb * P.nf + q) * (long long)P.in_box;
+        const long long jb = !P.in_field ? (long long)job * (long long)P.in_box
+                             : P.contig  ? (long long)P.nf * P.ext0 + (long long)job * E3
+                                         : (long long)P.nf * P.extpre[P.blocks[lb]] + (long long)q * E3;
         const TI *in = static_cast<const TI *>(P.in) + jb;
         for (int ch = tid; ch < kTile * cpr; ch += kProducers) {
           // exact: the fractional parts stay >= 0.5 / divisor away from an integer
@@ -563,8 +564,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       }
       if (c.valid) {
         if (!xrow) {
-          long long ib = P.in_field ? (long long)P.nf * P.extpre[c.b] + (long long)c.q * E3
-                                    : ((long long)c.lb * P.nf + c.q) * (long long)P.in_box;
+          long long ib = !P.in_field ? ((long long)c.lb * P.nf + c.q) * (long long)P.in_box
+                         : P.contig  ? (long long)P.nf * P.ext0 + ((long long)c.lb * P.nf + c.q) * E3
+                                     : (long long)P.nf * P.extpre[c.b] + (long long)c.q * E3;
           ib += (long long)(in_s1 + c.t1) * s_t1 + (long long)(in_s2 + c.t2) * s_t2;
           const TI *src = static_cast<const TI *>(P.in) + ib;
           for (int j = jq; j < E; j += 2) {
@@ -712,7 +714,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
         TO *fb = static_cast<TO *>(P.out);
         double *sb = P.scratch_out;
         if (wf)
-          fb += (long long)P.nf * P.nops * P.intpre[c.b] + ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
+          fb += (long long)P.nf * P.nops * (P.contig ? P.int0 + (long long)c.lb * n3 : P.intpre[c.b]) +
+                ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
                 (long long)(c.t1 - P.int_lo1) * f_t1 + (long long)(c.t2 - P.int_lo2) * f_t2;
         if (ws && halo)
           sb = P.halo_out + (((long long)c.b * P.nf + c.q) * (long long)(P.n1 * P.n2) + tile_pencil(P, tile, pl)) * 4;
@@ -1042,6 +1045,16 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
     base.out = out;
     base.seg_rows = N;
     base.kext = E;
+    {
+      const std::vector<int> &gb = B->groups[gi];
+      bool contig = true;
+      for (size_t k = 0; k < gb.size(); ++k)
+        if (gb[k] != gb[0] + (int)k) contig = false;
+      base.contig = contig ? 1 : 0;
+      base.b0 = gb[0];
+      base.ext0 = B->extpre[gb[0]];
+      base.int0 = B->intpre[gb[0]];
+    }
     base.nbr = B->d_nbr;
     base.halo_deg_mask = (B->s[0].present ? 1 : 0) | (B->s[1].present ? 2 : 0);
     auto run = [&](DenseParams P) -> cfd_status {
