@@ -344,9 +344,14 @@ __device__ __forceinline__ long long stride_of(int axis, long long s0, long long
 //               buffer (t_empty), rebuild the outputs and store them.
 // Every wait is bounded; a timeout latches CFD_ERR_TIMEOUT and ends the CTA.
 
-constexpr int kThreads = 512;
-constexpr int kProducers = 256;   // warps 0-7
-constexpr int kEpilogue = 256;    // warps 8-15
+#ifndef CFD_DENSE_PRODUCER_WARPS
+#define CFD_DENSE_PRODUCER_WARPS 8
+#endif
+constexpr int kProdWarps = CFD_DENSE_PRODUCER_WARPS;  // multiple of 4
+constexpr int kProducers = kProdWarps * 32;          // warps 0 .. kProdWarps-1
+constexpr int kParts = kProducers / 128;             // threads per pencil
+constexpr int kEpilogue = 256;                       // the next 8 warps
+constexpr int kThreads = kProducers + kEpilogue;
 constexpr int kPassCols = 160;    // TMEM columns per pass buffer ((L + 1) * R <= 160)
 constexpr int kPassBufs = 3;
 
@@ -375,8 +380,10 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
   }
   asm volatile("tcgen05.wait::ld.sync.aligned;");
   // the pass buffer can be reused as soon as every epilogue thread has its values
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t_empty_addr));
+  if (t_empty_addr) {  // last row group of the pass: the buffer can be reused
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t_empty_addr));
+  }
   if (!write_fin && !write_sc) return;  // a pencil outside the outputs of this pass
   // 16-byte vector stores where the output axis is contiguous (x): pencil rows are
   // 16-byte aligned (N and the output offsets are multiples of 16 elements)
@@ -422,15 +429,15 @@ __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr));
 }
-__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 256;"); }
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers)); }
 
 // Barrier of the 256 producer threads that also ORs a flag over them.
 __device__ __forceinline__ bool producer_any(bool v) {
   uint32_t r;
   asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
       : "=r"(r)
-      : "r"((uint32_t)v));
+      : "r"((uint32_t)v), "n"(kProducers));
   return r != 0;
 }
 
@@ -481,11 +488,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   uint16_t *sB = reinterpret_cast<uint16_t *>(smem + 2 * A_BYTES);
   TI *stg = reinterpret_cast<TI *>(smem + 2 * A_BYTES + 2 * B_PASS_BYTES);
   int *s_rowexp = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg) + kTile * PITCH_MAX * sizeof(TI));
-  int *s_emax = s_rowexp + 2 * 48;   // [2][128]
+  int *s_emax = s_rowexp + 2 * 48;   // [kParts][128]
   // Pencil scales of the last 8 tiles: producers run at most 5 tiles ahead of
   // the epilogue (two A buffers, three TMEM pass buffers), so a slot and its
   // mbarrier phase are never reused before the epilogue has read them.
-  int *s_etau = s_emax + 2 * kTile;  // [8][128] ring
+  int *s_etau = s_emax + kParts * kTile;  // [8][128] ring
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_etau + 8 * kTile);
   // bars: a_empty[2], t_full[3], t_empty[3], meta_full[8]
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 16);
@@ -533,14 +540,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   const uint32_t tmem = *tslot;
   bool failed = false;
 
-  if (warp < 8) {
+  if (warp < kProdWarps) {
     // ================================================================ producers (+ MMA issue by thread 0)
+    // kParts threads per pencil; part `half` splits K chunks half, half + kParts, ...
     const int pl = (warp & 3) * 32 + lane, half = warp >> 2;
+    constexpr int CPP = (NCH + kParts - 1) / kParts;  // K chunks per producer thread
     const float inv_n2 = 1.0f / (float)P.n2;
     const int cpr = E / VE;  // 16-byte chunks per pencil row (x axis); E * sizeof(TI) is a multiple of 16
     const float inv_cpr = 1.0f / (float)cpr;
     auto prefetch = [&](int tile) {
-      const int pp = tid & (kTile - 1), jq = tid >> 7;  // 2 threads per pencil
+      const int pp = tid & (kTile - 1), jq = tid >> 7;  // kParts threads per pencil
       const TileCoord c = tile_coord(P, tile, pp);
       if (xrow) {
         // x axis: the tile's pencil rows, 16-byte chunks, consecutive threads on consecutive
@@ -569,12 +578,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
                                      : (long long)P.nf * P.extpre[c.b] + (long long)c.q * E3;
           ib += (long long)(in_s1 + c.t1) * s_t1 + (long long)(in_s2 + c.t2) * s_t2;
           const TI *src = static_cast<const TI *>(P.in) + ib;
-          for (int j = jq; j < E; j += 2) {
+          for (int j = jq; j < E; j += kParts) {
             if constexpr (sizeof(TI) == 8) cp_async8(stg + pp * pitch + j, src + (long long)j * s_ax);
             else cp_async4(stg + pp * pitch + j, src + (long long)j * s_ax);
           }
         }
-        if (P.halo_in) {
+        if (P.halo_in && jq < 2) {
           // previous iterate of the neighbours at k^c: d_lo from the lower neighbour's row N-2,
           // d_hi from the upper neighbour's row 1 (same pencil), per degree
           const int ez = P.axis == 0, ey = P.axis == 1, ex = P.axis == 2;
@@ -598,20 +607,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       const TileCoord c = tile_coord(P, tile, pl);
       asm volatile("cp.async.wait_all;");
       producer_sync();
-      TI v[NCH / 2][8];
+      TI v[CPP][8];
       int em = 0;
 #pragma unroll
-      for (int h = 0; h < NCH / 2; ++h) {
+      for (int h = 0; h < CPP; ++h) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int j = (half * (NCH / 2) + h) * 8 + k;
+          const int j = (half + kParts * h) * 8 + k;
           v[h][k] = (j < P.kext && c.valid) ? stg[pl * pitch + j] : TI(0);
           em = max(em, biased_exp(v[h][k]));
         }
       }
       s_emax[half * kTile + pl] = em;
       producer_sync();  // exponents exchanged, staging fully read
-      const int emax = max(s_emax[pl], s_emax[kTile + pl]);
+      int emax = s_emax[pl];
+#pragma unroll
+      for (int q = 1; q < kParts; ++q) emax = max(emax, s_emax[q * kTile + pl]);
       if (tile + (int)gridDim.x < P.ntiles) prefetch(tile + gridDim.x);
       // A[buf] must be free: the MMAs of its previous use have completed
       const bool ok = use == 0 || mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1));
@@ -620,8 +631,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       uint16_t *Ab = sA + (size_t)buf * (A_BYTES / 2);
       const int row_group = pl >> 3, row_in = pl & 7;
 #pragma unroll
-      for (int h = 0; h < NCH / 2; ++h) {
-        const int ch = half * (NCH / 2) + h;
+      for (int h = 0; h < CPP; ++h) {
+        const int ch = half + kParts * h;
+        if (ch >= NCH) break;
         uint32_t w[S][4];
         if (ch * 8 >= P.kext) {  // K padding: zero digits (warp-uniform branch)
 #pragma unroll
@@ -685,7 +697,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
     asm volatile("cp.async.wait_all;");
   } else {
     // ================================================================ epilogue
-    const int quad = warp & 3, ehalf = (warp - 8) >> 2;
+    const int quad = warp & 3, ehalf = (warp - kProdWarps) >> 2;
     const int pl = quad * 32 + lane;
     const long long n3 = (long long)N * N * N;
     const long long f_t1 = stride_of(P.t1, (long long)N * N, N), f_t2 = stride_of(P.t2, (long long)N * N, N),
@@ -726,10 +738,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
         const int srows = halo ? 4 : 1 << 30;
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
         const int *rexp = s_rowexp + ps * 48 + r0;
+        // rows in groups of 8 (fewer live registers); the pass buffer is released after the last group
         if (RH == 16)
-          epilogue_rows<16, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows, P.xvec != 0);
-        else
-          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, t_empty(tb), srows, P.xvec != 0);
+          epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u, srows,
+                                      P.xvec != 0);
+        epilogue_rows<8, L + 1, TO>(taddr + (RH - 8), (uint32_t)R, etau, rexp + (RH - 8), fb, f_ax, sb, sstr, wf, ws,
+                                    i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0);
       }
     }
   }
@@ -958,7 +972,7 @@ int levels_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 4 : 1; }
 // one CTA (holding all 512 TMEM columns) occupies an SM.
 size_t dense_smem(int KP, int S, int rows, size_t elem) {
   const size_t need = 2 * (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2 +
-                      (size_t)kTile * (KP + 16 / elem) * elem + (2 * 48 + 2 * kTile + 8 * kTile) * 4 + 16 * 8 + 64;
+                      (size_t)kTile * (KP + 16 / elem) * elem + (2 * 48 + kParts * kTile + 8 * kTile) * 4 + 16 * 8 + 64;
   return std::max(need, (size_t)116 * 1024);
 }
 
