@@ -1,5 +1,7 @@
 // Dense per-block operator D = A^-1 B on the tensor cores (see dense_tc.cu).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
+
 #include "cfd_internal.h"
 
 namespace cfd {
@@ -39,6 +41,10 @@ struct DenseParams {
   // (no dependent table loads in the tile loop)
   int contig, b0;
   long long ext0, int0;      // extpre[b0], intpre[b0]
+  // TMA staging of the tile's pencils (0: cp.async path): 1 x rows (SWIZZLE_128B boxes of 128
+  // bytes along x), 2 y columns (box [t1][y][x]), 3 z columns (box [z][t1][x])
+  int tma_kind, tma_boxes, tma_bytes, tma_zstep;  // zstep: z planes per job in the tensor map
+  alignas(64) CUtensorMap tmap;
   int *status;
 };
 

@@ -471,36 +471,43 @@ __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, 
 }
 
 template <typename TI, typename TO, int KP, int S, int L>
-__global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
+__global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int A_BYTES = S * kTile * KP * 2;
-  // Staging row pitch (elements): odd for the y/z axes (one element per thread and copy,
-  // spread over the banks); for the x axis, where a pencil is a contiguous row copied in
+  // cp.async staging row pitch (elements): odd for the y/z axes (one element per thread and
+  // copy, spread over the banks); for the x axis, where a pencil is a contiguous row copied in
   // 16-byte chunks, a pitch whose rows stay 16-byte aligned.
   constexpr int VE = 16 / sizeof(TI);  // elements per 16-byte chunk
-  constexpr int PITCH_MAX = KP + VE;
+  constexpr int XB = 128 / sizeof(TI); // elements per 128-byte swizzled TMA row (x rows)
   const bool xrow = P.xrow != 0;
   const int pitch = xrow ? KP + VE : KP + 1;
   constexpr int NCH = KP / 8;    // 8-value K chunks per pencil
   const int R = P.rows;
   const int B_PASS_BYTES = S * R * KP * 2;
+  const int kind = P.tma_kind;
   uint16_t *sA = reinterpret_cast<uint16_t *>(smem);  // [2][S][128][KP]
   uint16_t *sB = reinterpret_cast<uint16_t *>(smem + 2 * A_BYTES);
-  TI *stg = reinterpret_cast<TI *>(smem + 2 * A_BYTES + 2 * B_PASS_BYTES);
-  int *s_rowexp = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(stg) + kTile * PITCH_MAX * sizeof(TI));
-  int *s_emax = s_rowexp + 2 * 48;   // [kParts][128]
+  // staging, 1024-byte aligned (128-byte swizzle atoms)
+  const int stg_off = (2 * A_BYTES + 2 * B_PASS_BYTES + 1023) & ~1023;
+  TI *stg = reinterpret_cast<TI *>(smem + stg_off);
+  const int stg_bytes = max(kTile * (KP + VE) * (int)sizeof(TI), P.tma_boxes * kTile * 128);
+  int *s_rowexp = reinterpret_cast<int *>(smem + stg_off + stg_bytes);
+  int *s_emax = s_rowexp + 2 * 48;   // [2 tiles][kParts][128]
   // Pencil scales of the last 8 tiles: producers run at most 5 tiles ahead of
   // the epilogue (two A buffers, three TMEM pass buffers), so a slot and its
   // mbarrier phase are never reused before the epilogue has read them.
-  int *s_etau = s_emax + kParts * kTile;  // [8][128] ring
+  int *s_etau = s_emax + 2 * kParts * kTile;  // [8][128] ring
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_etau + 8 * kTile);
-  // bars: a_empty[2], t_full[3], t_empty[3], meta_full[8]
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 16);
+  // bars: a_empty[2], t_full[3], t_empty[3], meta_full[8], a_full[2], stg_full (thread 0 issues
+  // the MMAs after the a_full wait; the other producers go on to the next tile)
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 24);
   const uint32_t bar0 = smem_u32(bars);
   auto a_empty = [&](int i) { return bar0 + 8u * (uint32_t)i; };
   auto t_full = [&](int i) { return bar0 + 8u * (uint32_t)(2 + i); };
   auto t_empty = [&](int i) { return bar0 + 8u * (uint32_t)(5 + i); };
   auto meta_full = [&](int i) { return bar0 + 8u * (uint32_t)(8 + i); };
+  auto a_full = [&](int i) { return bar0 + 8u * (uint32_t)(16 + i); };
+  const uint32_t stg_full = bar0 + 8u * 18u;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = P.N, g = P.g, E = N + 2 * g;
@@ -511,9 +518,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) mbar_init(a_empty(i), 1);
+    for (int i = 0; i < 2; ++i) { mbar_init(a_empty(i), 1); mbar_init(a_full(i), kProducers); }
     for (int i = 0; i < kPassBufs; ++i) { mbar_init(t_full(i), 1); mbar_init(t_empty(i), kEpilogue); }
     for (int i = 0; i < 8; ++i) mbar_init(meta_full(i), kProducers);
+    mbar_init(stg_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   const int SR = P.seg_rows;
@@ -541,13 +549,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
   bool failed = false;
 
   if (warp < kProdWarps) {
-    // ================================================================ producers (+ MMA issue by thread 0)
+    // ================================================================ producers
     // kParts threads per pencil; part `half` splits K chunks half, half + kParts, ...
     const int pl = (warp & 3) * 32 + lane, half = warp >> 2;
     constexpr int CPP = (NCH + kParts - 1) / kParts;  // K chunks per producer thread
     const float inv_n2 = 1.0f / (float)P.n2;
     const int cpr = E / VE;  // 16-byte chunks per pencil row (x axis); E * sizeof(TI) is a multiple of 16
     const float inv_cpr = 1.0f / (float)cpr;
+    // TMA: one thread posts the expected bytes and issues the box copies of a tile
+    bool tma_pending = false;
+    auto tma_issue = [&](int tile) {
+      const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+      const int t1_0 = tj * (kTile / P.n2);
+      const uint64_t tmap = reinterpret_cast<uint64_t>(&P.tmap);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(stg_full), "r"(P.tma_bytes)
+                   : "memory");
+      // box origin in (x, y, z) of the tensor map: z also steps over the jobs
+      const int cz = P.in_start[0] + job * P.tma_zstep + (P.t1 == 0 ? t1_0 : 0);
+      const int cy = P.in_start[1] + (P.t1 == 1 ? t1_0 : 0);
+      for (int bx = 0; bx < P.tma_boxes; ++bx) {
+        const uint32_t dst = smem_u32(stg) + (uint32_t)(bx * kTile * 128);
+        const int cx = P.in_start[2] + bx * XB;
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(dst),
+            "l"(tmap), "r"(cx), "r"(cy), "r"(cz), "r"(stg_full)
+            : "memory");
+      }
+      tma_pending = true;
+    };
     auto prefetch = [&](int tile) {
       const int pp = tid & (kTile - 1), jq = tid >> 7;  // kParts threads per pencil
       const TileCoord c = tile_coord(P, tile, pp);
@@ -598,15 +628,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       }
       asm volatile("cp.async.commit_group;");
     };
+    // staging address of element j of this thread's pencil
+    const int n2 = P.n2;
+    const int col_base = kind == 2 ? (pl / n2) * E * n2 + (pl % n2) : pl;       // kinds 2, 3
+    const int col_step = kind == 2 ? n2 : kTile;
+    auto stg_index = [&](int j) -> int {
+      if (kind == 0) return pl * pitch + j;
+      if (kind == 1) {  // 128-byte rows, 16-byte chunk index XOR (row mod 8)
+        const int bx = j / XB, xo = j - bx * XB;
+        return bx * (kTile * XB) + pl * XB + (((xo / VE) ^ (pl & 7)) * VE) + (xo % VE);
+      }
+      return col_base + j * col_step;
+    };
     const uint32_t lbo = 128, sbo = KP * 16;
     int it = 0, pit = 0;
+    uint32_t last_bar = 0, last_par = 0;  // thread 0: the last MMA commit
     int tile = blockIdx.x;
-    if (tile < P.ntiles) prefetch(tile);
+    if (tile < P.ntiles) {
+      if (kind) { if (tid == 0) tma_issue(tile); }
+      else prefetch(tile);
+    }
     for (; tile < P.ntiles; tile += gridDim.x, ++it) {
       const int buf = it & 1, use = it >> 1;
       const TileCoord c = tile_coord(P, tile, pl);
-      asm volatile("cp.async.wait_all;");
-      producer_sync();
+      if (kind) {
+        if (!mbar_wait_bounded(stg_full, (uint32_t)(it & 1))) failed = true;
+        else if (tid == 0) tma_pending = false;
+      } else {
+        asm volatile("cp.async.wait_all;");
+        producer_sync();
+      }
       TI v[CPP][8];
       int em = 0;
 #pragma unroll
@@ -614,19 +665,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int j = (half + kParts * h) * 8 + k;
-          v[h][k] = (j < P.kext && c.valid) ? stg[pl * pitch + j] : TI(0);
+          v[h][k] = (j < P.kext && c.valid) ? stg[stg_index(j)] : TI(0);
           em = max(em, biased_exp(v[h][k]));
         }
       }
-      s_emax[half * kTile + pl] = em;
-      producer_sync();  // exponents exchanged, staging fully read
-      int emax = s_emax[pl];
+      int *se = s_emax + (it & 1) * (kParts * kTile);
+      se[half * kTile + pl] = em;
+      // staging fully read, exponents exchanged; a failed wait anywhere ends every producer here
+      if (producer_any(failed)) { failed = true; break; }
+      int emax = se[pl];
 #pragma unroll
-      for (int q = 1; q < kParts; ++q) emax = max(emax, s_emax[q * kTile + pl]);
-      if (tile + (int)gridDim.x < P.ntiles) prefetch(tile + gridDim.x);
+      for (int q = 1; q < kParts; ++q) emax = max(emax, se[q * kTile + pl]);
+      if (tile + (int)gridDim.x < P.ntiles) {
+        if (kind) { if (tid == 0) tma_issue(tile + gridDim.x); }
+        else prefetch(tile + gridDim.x);
+      }
       // A[buf] must be free: the MMAs of its previous use have completed
-      const bool ok = use == 0 || mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1));
-      if (producer_any(!ok || failed)) { failed = true; break; }
+      if (use > 0 && !mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1))) failed = true;
       if (half == 0) s_etau[(it & 7) * kTile + pl] = tau_exp(emax, TI(0));
       uint16_t *Ab = sA + (size_t)buf * (A_BYTES / 2);
       const int row_group = pl >> 3, row_in = pl & 7;
@@ -661,11 +716,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
       }
       asm volatile("fence.proxy.async.shared::cta;");
       mbar_arrive(meta_full(it & 7));
-      producer_sync();  // A[buf] complete
+      mbar_arrive(a_full(buf));  // A[buf] written by this thread
       if (tid == 0) {
+        // MMA issue: once every producer has written A[buf] (the others go on to the next tile)
+        if (!mbar_wait_bounded(a_full(buf), (uint32_t)(use & 1))) failed = true;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t a0 = smem_u32(sA) + (uint32_t)(buf * A_BYTES);
-        for (int ps = 0; ps < P.passes; ++ps, ++pit) {
+        for (int ps = 0; ps < P.passes && !failed; ++ps, ++pit) {
           const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
           if (tuse > 0 && !mbar_wait_bounded(t_empty(tb), (uint32_t)((tuse - 1) & 1))) { failed = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;");
@@ -687,14 +744,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               t_full(tb)));
         }
-        if (!failed)
+        if (!failed) {
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               a_empty(buf)));
-      } else {
-        pit += P.passes;
+          last_bar = a_empty(buf);
+          last_par = (uint32_t)(use & 1);
+        }
       }
     }
     asm volatile("cp.async.wait_all;");
+    if (tid == 0) {
+      // a TMA copy still in flight after a failure completes before the CTA leaves, and the
+      // MMAs issued last complete before TMEM is released
+      if (tma_pending) mbar_wait_bounded(stg_full, (uint32_t)(it & 1));
+      if (last_bar) mbar_wait_bounded(last_bar, last_par);
+    }
   } else {
     // ================================================================ epilogue
     const int quad = warp & 3, ehalf = (warp - kProdWarps) >> 2;
@@ -756,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const DenseParams P) {
 
 template <typename TI, typename TO, int KP>
 cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned grid, cudaStream_t st) {
-  void (*fn)(const DenseParams);
+  void (*fn)(const __grid_constant__ DenseParams);
   if (S == 5 && L == 4) fn = k_dense<TI, TO, KP, 5, 4>;
   else if (S == 2 && L == 1) fn = k_dense<TI, TO, KP, 2, 1>;
   else { set_error("dense: unsupported slice configuration"); return CFD_ERR_UNSUPPORTED; }
@@ -970,10 +1034,79 @@ int levels_of(cfd_precision p) { return p == CFD_TC_BF16_EXACT ? 4 : 1; }
 // Shared memory per CTA: two A digit buffers, B digits of two passes, the
 // input staging tile, row exponents, exponent exchange, etau ring, barriers.  At least 116 KB so that
 // one CTA (holding all 512 TMEM columns) occupies an SM.
-size_t dense_smem(int KP, int S, int rows, size_t elem) {
-  const size_t need = 2 * (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2 +
-                      (size_t)kTile * (KP + 16 / elem) * elem + (2 * 48 + kParts * kTile + 8 * kTile) * 4 + 16 * 8 + 64;
+size_t dense_smem(int KP, int S, int rows, size_t elem, int tma_boxes) {
+  const size_t ab = 2 * (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2;
+  const size_t stg = std::max((size_t)kTile * (KP + 16 / elem) * elem, (size_t)tma_boxes * kTile * 128);
+  const size_t need = ((ab + 1023) & ~(size_t)1023) + stg + (2 * 48 + 2 * kParts * kTile + 8 * kTile) * 4 + 24 * 8 + 64;
   return std::max(need, (size_t)116 * 1024);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// TMA staging for a stage whose 128-pencil tiles are boxes of the input: pencils along x
+// (x rows, 128-byte swizzled boxes) or along y / z (one box of the whole columns).  Falls
+// back to the cp.async path (tma_kind 0) when a box or alignment rule does not hold.
+void plan_tma(DenseParams &P, size_t elem) {
+  P.tma_kind = 0;
+  P.tma_boxes = 0;
+  if (P.halo_in) return;  // iterated passes add halo columns per pencil
+  const int n2 = P.n2, E = P.N + 2 * P.g;
+  if ((n2 != 16 && n2 != 32) || (P.n1 * n2) % kTile != 0) return;
+  if (P.in_field && !P.contig) return;
+  const int d0 = P.in_dims[0], d1 = P.in_dims[1], d2 = P.in_dims[2];
+  if (P.in_dims[P.axis] != E) return;
+  const char *base = static_cast<const char *>(P.in) + (P.in_field ? (size_t)P.nf * P.ext0 * elem : 0);
+  if (((uintptr_t)base & 15) || ((size_t)d2 * elem) % 16 || ((size_t)d1 * d2 * elem) % 16) return;
+  if (((size_t)P.in_start[2] * elem) % 16) return;
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return;
+  const int njobs = P.nblk * P.nf;
+  const cuuint64_t gdim[3] = {(cuuint64_t)d2, (cuuint64_t)d1, (cuuint64_t)d0 * njobs};
+  const cuuint64_t gstr[2] = {(cuuint64_t)d2 * elem, (cuuint64_t)d1 * d2 * elem};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  cuuint32_t box[3];
+  int kind, boxes;
+  CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE;
+  const int xb = (int)(128 / elem);
+  if (P.axis == 2) {  // t1 = z, t2 = y
+    kind = 1;
+    boxes = (E + xb - 1) / xb;
+    box[0] = (cuuint32_t)xb; box[1] = (cuuint32_t)n2; box[2] = (cuuint32_t)(kTile / n2);
+    swz = CU_TENSOR_MAP_SWIZZLE_128B;
+  } else if (P.axis == 1) {  // t1 = z, t2 = x
+    kind = 2;
+    boxes = 1;
+    box[0] = (cuuint32_t)n2; box[1] = (cuuint32_t)E; box[2] = (cuuint32_t)(kTile / n2);
+  } else {  // t1 = y, t2 = x
+    kind = 3;
+    boxes = 1;
+    box[0] = (cuuint32_t)n2; box[1] = (cuuint32_t)(kTile / n2); box[2] = (cuuint32_t)E;
+  }
+  const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  if (enc(&P.tmap, dt, 3, const_cast<char *>(base), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return;
+  P.tma_kind = kind;
+  P.tma_boxes = boxes;
+  P.tma_bytes = (int)(box[0] * box[1] * box[2] * elem) * boxes;
+  P.tma_zstep = d0;
 }
 
 }  // namespace
@@ -1081,7 +1214,9 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       P.ntiles = P.tiles_per_job * P.nblk * P.nf;
       const unsigned grid = (unsigned)std::min(P.ntiles, sms);
       const bool f32 = B->dtype == CFD_F32;
-      const size_t smem = dense_smem(G.Kp, S, P.rows, (P.in_field && f32) ? 4 : 8);
+      const size_t ein_b = (P.in_field && f32) ? 4 : 8;
+      plan_tma(P, ein_b);
+      const size_t smem = dense_smem(G.Kp, S, P.rows, ein_b, P.tma_boxes);
       if (!P.in_field)
         return f32 ? launch_types<double, float>(P, G.Kp, S, L, smem, grid, st)
                    : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
