@@ -44,7 +44,12 @@ struct DenseParams {
   // TMA staging of the tile's pencils (0: cp.async path): 1 x rows (SWIZZLE_128B boxes of 128
   // bytes along x), 2 y columns (box [t1][y][x]), 3 z columns (box [z][t1][x])
   int tma_kind, tma_boxes, tma_bytes, tma_zstep;  // zstep: z planes per job in the tensor map
-  alignas(64) CUtensorMap tmap;
+  // Intermediate written on interior pencils only: each value within g of an x (and, with
+  // ghost_y, a y) face is also written into the face neighbour's ghost column of the same box.
+  // nl: [nblk][4] local indices of the x-, x+, y-, y+ face neighbours.
+  int ghost_x, ghost_y;
+  const int *nl;
+  CUtensorMap tmap;          // (the type carries its own 128-byte alignment)
   int *status;
 };
 

@@ -359,7 +359,8 @@ template <int RH, int LEV, typename TO>
 __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int etau, const int *rowexp,
                                               TO *fin_base, long long fin_stride, double *sc_base,
                                               long long sc_stride, bool write_fin, bool write_sc, int i0,
-                                              uint32_t t_empty_addr, int sc_rows, bool vec) {
+                                              uint32_t t_empty_addr, int sc_rows, bool vec, double *sc_x,
+                                              double *sc_y) {
   uint32_t acc[LEV][RH];
 #pragma unroll
   for (int k = 0; k < LEV; ++k) {
@@ -407,10 +408,19 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
       if constexpr (sizeof(TO) == 8) {
         const double dv = scaled_int_to_double(Y, ex);
         o[u] = dv;
-        if (write_sc && i < sc_rows) sc_base[i * sc_stride] = dv;
+        if (write_sc && i < sc_rows) {
+          sc_base[i * sc_stride] = dv;
+          if (sc_x) sc_x[i * sc_stride] = dv;  // the face neighbour's ghost column
+          if (sc_y) sc_y[i * sc_stride] = dv;
+        }
       } else {
         o[u] = scaled_int_to_float(Y, ex);
-        if (write_sc && i < sc_rows) sc_base[i * sc_stride] = scaled_int_to_double(Y, ex);
+        if (write_sc && i < sc_rows) {
+          const double dv = scaled_int_to_double(Y, ex);
+          sc_base[i * sc_stride] = dv;
+          if (sc_x) sc_x[i * sc_stride] = dv;
+          if (sc_y) sc_y[i * sc_stride] = dv;
+        }
       }
       if (write_fin && !vec) fin_base[i * fin_stride] = o[u];
     }
@@ -800,14 +810,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
                 (long long)(sc_s2 + c.t2) * c_t2;
         const long long sstr = halo ? 1 : c_ax;
         const int srows = halo ? 4 : 1 << 30;
+        // interior pencils near an x (y) face also fill the neighbour's ghost column (row)
+        double *gx = nullptr, *gyp = nullptr;
+        if (ws && !halo && P.ghost_x) {
+          const int xs = sc_s2 + c.t2;  // t2 is the x axis in the stages that write intermediates
+          const long long jump = (long long)P.nf * (long long)P.sc_box;
+          if (xs < 2 * g) gx = sb + (long long)(P.nl[c.lb * 4 + 0] - c.lb) * jump + N;
+          else if (xs >= N) gx = sb + (long long)(P.nl[c.lb * 4 + 1] - c.lb) * jump - N;
+          if (P.ghost_y) {
+            const int ys = sc_s1 + c.t1;  // t1 is the y axis (z stage)
+            if (ys < 2 * g) gyp = sb + (long long)(P.nl[c.lb * 4 + 2] - c.lb) * jump + (long long)N * ss1;
+            else if (ys >= N) gyp = sb + (long long)(P.nl[c.lb * 4 + 3] - c.lb) * jump - (long long)N * ss1;
+          }
+        }
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
         const int *rexp = s_rowexp + ps * 48 + r0;
         // rows in groups of 8 (fewer live registers); the pass buffer is released after the last group
         if (RH == 16)
           epilogue_rows<8, L + 1, TO>(taddr, (uint32_t)R, etau, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u, srows,
-                                      P.xvec != 0);
+                                      P.xvec != 0, gx, gyp);
         epilogue_rows<8, L + 1, TO>(taddr + (RH - 8), (uint32_t)R, etau, rexp + (RH - 8), fb, f_ax, sb, sstr, wf, ws,
-                                    i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0);
+                                    i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0, gx, gyp);
       }
     }
   }
@@ -853,45 +876,6 @@ cfd_status launch_types(const DenseParams &P, int KP, int S, int L, size_t smem,
   }
 }
 
-// Ghost columns of an FP64 intermediate G = D_j f (box [N][d1][E], x fastest) copied
-// from the face neighbours' interior values: part A the x ghosts of the N rows
-// y = ylo..ylo+N-1, part B (do_y) the y ghosts of the interior x columns.  On a
-// same-size neighbour the copied value is the one local evaluation on the ghost
-// rows would produce (identical input data and arithmetic).
-template <int NC, int GC>
-__global__ void k_scratch_halo(double *G, const int *__restrict__ blocks, const int *__restrict__ lidx,
-                               const int *__restrict__ nbr, int nf, int N_, int g_, int d1, int ylo, int do_y,
-                               unsigned long long box) {
-  const int N = NC ? NC : N_, g = NC ? GC : g_;  // constant sizes turn the divisions into multiply-shifts
-  const int E = N + 2 * g, G2 = 2 * g;
-  const int nA = N * N * G2, nB = do_y ? N * G2 * N : 0;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nA + nB) return;
-  const int job = blockIdx.y, lb = job / nf, q = job - lb * nf;
-  const int b = blocks[lb];
-  int z, y, x, dy = 0, dx = 0;
-  if (idx < nA) {
-    const int r = idx / G2, xx = idx - r * G2;
-    z = r / N;
-    y = ylo + (r - z * N);
-    x = xx < g ? xx : xx + N;
-    dx = xx < g ? -1 : 1;
-  } else {
-    const int r = idx - nA, row = r / N;
-    x = g + (r - row * N);
-    z = row / G2;
-    const int yy = row - z * G2;
-    y = yy < g ? yy : yy + N;
-    dy = yy < g ? -1 : 1;
-  }
-  const int nb = nbr[b * 26 + dir_index_dev(0, dy, dx)];
-  if (nb < 0) return;
-  const int ln = lidx[nb];
-  const long long dst = ((long long)lb * nf + q) * (long long)box + ((long long)z * d1 + y) * E + x;
-  const long long src = ((long long)ln * nf + q) * (long long)box + ((long long)z * d1 + (y - dy * N)) * E + (x - dx * N);
-  G[dst] = G[src];
-}
-
 // ------------------------------------------------------------------ host planning
 
 struct DenseOp {        // one (group, axis, degree) operator
@@ -909,11 +893,11 @@ struct DenseGroup {
   DenseOp halo0[3];      // rows 1 and N-2 of [0]D per degree (16 rows), unscaled
   DenseOp haloI[3];      // rows 1 and N-2 of the iterated operator (16 rows), unscaled
   bool faces_x = false, faces_y = false;  // every block has both x (y) face neighbours
+  int *d_nl = nullptr;   // device [nblk][4]: local indices of the x-, x+, y-, y+ neighbours
 };
 
 struct DenseState {
   std::vector<DenseGroup> groups;
-  int *d_lidx = nullptr;  // device: block id -> index within its size group
 };
 
 DenseState *state_of(cfd_blocks_s *B) { return reinterpret_cast<DenseState *>(B->dense_state); }
@@ -1009,9 +993,14 @@ cfd_status dense_bind(cfd_blocks_s *B) {
     {
       auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
       G.faces_x = G.faces_y = true;
+      // both face neighbours present and reciprocal (the neighbour's opposite face is this block)
+      auto face = [&](int b, int dy, int dx) {
+        const int nb = B->nbr[b * 26 + di(0, dy, dx)];
+        return nb >= 0 && B->nbr[nb * 26 + di(0, -dy, -dx)] == b;
+      };
       for (int b : B->groups[gi]) {
-        if (B->nbr[b * 26 + di(0, 0, -1)] < 0 || B->nbr[b * 26 + di(0, 0, 1)] < 0) G.faces_x = false;
-        if (B->nbr[b * 26 + di(0, -1, 0)] < 0 || B->nbr[b * 26 + di(0, 1, 0)] < 0) G.faces_y = false;
+        if (!face(b, 0, -1) || !face(b, 0, 1)) G.faces_x = false;
+        if (!face(b, -1, 0) || !face(b, 1, 0)) G.faces_y = false;
       }
     }
     st->groups.push_back(G);
@@ -1019,11 +1008,28 @@ cfd_status dense_bind(cfd_blocks_s *B) {
   std::vector<int> lidx(B->nblocks, 0);
   for (size_t gi = 0; gi < B->groups.size(); ++gi)
     for (size_t k = 0; k < B->groups[gi].size(); ++k) lidx[B->groups[gi][k]] = (int)k;
-  cfd_status s = cuda_fail(cudaMalloc((void **)&st->d_lidx, lidx.size() * 4), "cudaMalloc");
-  if (st->d_lidx) B->d_dense_ptrs.push_back(st->d_lidx);
-  if (s == CFD_OK)
-    s = cuda_fail(cudaMemcpy(st->d_lidx, lidx.data(), lidx.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-  return s;
+  for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+    DenseGroup &G = st->groups[gi];
+    if (!G.faces_x) continue;
+    auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
+    const std::vector<int> &gb = B->groups[gi];
+    std::vector<int> nl(gb.size() * 4, -1);
+    for (size_t k = 0; k < gb.size(); ++k) {
+      const int b = gb[k];
+      const int nx0 = B->nbr[b * 26 + di(0, 0, -1)], nx1 = B->nbr[b * 26 + di(0, 0, 1)];
+      nl[k * 4 + 0] = lidx[nx0];
+      nl[k * 4 + 1] = lidx[nx1];
+      if (G.faces_y) {
+        nl[k * 4 + 2] = lidx[B->nbr[b * 26 + di(0, -1, 0)]];
+        nl[k * 4 + 3] = lidx[B->nbr[b * 26 + di(0, 1, 0)]];
+      }
+    }
+    cfd_status s = cuda_fail(cudaMalloc((void **)&G.d_nl, nl.size() * 4), "cudaMalloc");
+    if (G.d_nl) B->d_dense_ptrs.push_back(G.d_nl);
+    if (s == CFD_OK) s = cuda_fail(cudaMemcpy(G.d_nl, nl.data(), nl.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (s != CFD_OK) return s;
+  }
+  return CFD_OK;
 }
 
 namespace {
@@ -1304,24 +1310,12 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       if ((s = run_stage(P, 2)) != CFD_OK) return s;
     }
     // S_y: D_y on (z interior, x extended if d_xy) -> d_y, d_yy, and G_y = D_y f for d_xy
-    // With face neighbours along x (and y), the intermediates are computed on the
-    // interior pencils only and their ghost columns copied from the neighbours.
-    auto scratch_halo = [&](double *Gs, int d1, int ylo, int do_y, unsigned long long box) -> cfd_status {
-      const int n = N * N * 2 * g * (do_y ? 2 : 1);
-      dim3 grid((unsigned)((n + 255) / 256), (unsigned)(base.nblk * nf));
-      launch_begin(KF_HALO, st);
-      auto kern = k_scratch_halo<0, 0>;
-      if (N == 32 && g == 4) kern = k_scratch_halo<32, 4>;
-      else if (N == 16 && g == 4) kern = k_scratch_halo<16, 4>;
-      else if (N == 32 && g == 5) kern = k_scratch_halo<32, 5>;
-      else if (N == 16 && g == 5) kern = k_scratch_halo<16, 5>;
-      kern<<<grid, 256, 0, st>>>(Gs, base.blocks, ds->d_lidx, B->d_nbr, nf, N, g, d1, ylo, do_y, box);
-      launch_end(KF_HALO, st);
-      return cuda_fail(cudaGetLastError(), "k_scratch_halo launch");
-    };
+    // With face neighbours along x (and y), the intermediates are computed on the interior
+    // pencils only; the epilogue also writes each value within g of a face into the face
+    // neighbour's ghost column (row), which is what local evaluation there would give.
     if (ody >= 0 || odyy >= 0 || odxy >= 0) {
       const bool ext = odxy >= 0;
-      const bool copy = ext && G.faces_x;  // interior pencils + ghost-column copy
+      const bool copy = ext && G.faces_x && N >= 2 * g;  // interior pencils + ghost columns from the epilogue
       DenseParams P = field_stage(1, 0, 2, g, N, (ext && !copy) ? 0 : g, (ext && !copy) ? E : N);
       const int m1 = (ody >= 0 && ext) ? 3 : (ody >= 0 ? 0 : (ext ? 2 : -1));
       set_segments(P, 1, m1, ody, odyy >= 0 ? 0 : -1, odyy);
@@ -1330,14 +1324,15 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.sc_box = (unsigned long long)N * N * E;
         P.sc_dims[0] = N; P.sc_dims[1] = N; P.sc_dims[2] = E;
         P.sc_start[0] = 0; P.sc_start[1] = 0; P.sc_start[2] = copy ? g : 0;
+        P.ghost_x = copy ? 1 : 0;
+        P.nl = G.d_nl;
       }
       if ((s = run_stage(P, 1)) != CFD_OK) return s;
-      if (copy && (s = scratch_halo(gy, N, 0, 0, P.sc_box)) != CFD_OK) return s;
     }
     // S_z: D_z on (y, x) extended for d_xz / d_yz -> d_z, d_zz, and G_z = D_z f
     if (odz >= 0 || odzz >= 0 || odxz >= 0 || odyz >= 0) {
       const bool ext = odxz >= 0 || odyz >= 0;
-      const bool copy = ext && G.faces_x && G.faces_y;
+      const bool copy = ext && G.faces_x && G.faces_y && N >= 2 * g;
       const bool wide = ext && !copy;
       DenseParams P = field_stage(0, 1, 2, wide ? 0 : g, wide ? E : N, wide ? 0 : g, wide ? E : N);
       const int m1 = (odz >= 0 && ext) ? 3 : (odz >= 0 ? 0 : (ext ? 2 : -1));
@@ -1347,9 +1342,11 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.sc_box = (unsigned long long)N * E * E;
         P.sc_dims[0] = N; P.sc_dims[1] = E; P.sc_dims[2] = E;
         P.sc_start[0] = 0; P.sc_start[1] = copy ? g : 0; P.sc_start[2] = copy ? g : 0;
+        P.ghost_x = P.ghost_y = copy ? 1 : 0;
+        P.nl = G.d_nl;
       }
       if ((s = run_stage(P, 0)) != CFD_OK) return s;
-      if (copy && (s = scratch_halo(gz, E, g, 1, P.sc_box)) != CFD_OK) return s;
+
     }
     // T stages on the intermediates (one order of the mixed product: the closed
     // block operators of two axes commute, D_i D_j = D_j D_i)
