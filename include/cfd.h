@@ -219,6 +219,43 @@ cfd_status cfd_wave_workspace(cfd_blocks_t blocks, cfd_precision prec, int n_ite
 cfd_status cfd_wave_rk_step(cfd_blocks_t blocks, void *phi, void *K, double dt, cfd_precision prec,
                             int n_iter, void *work, size_t work_bytes, void *stream);
 
+/*
+ * Coefficients of a two-register (2S) low-storage Runge-Kutta method with
+ * `stages` stages (1..8).  Per stage i, with S1 the state and S2 a second
+ * register that is zero on entry:
+ *     S2 <- S2 + delta[i] S1
+ *     S1 <- gamma1[i] S1 + gamma2[i] S2 + beta[i] dt F(S1 before this stage)
+ * The paper's host code evolves with the 4-stage 4th-order RK4()4[2S] method
+ * of this form (Sec. "Z4c: system description"); it prints no coefficients,
+ * so the caller supplies them.  The arrays are host memory, read during the
+ * call only.
+ */
+typedef struct {
+  int stages;
+  const double *gamma1, *gamma2, *beta, *delta;
+} cfd_lsrk_desc;
+
+/* Device workspace of cfd_wave_lsrk_step (bytes). */
+cfd_status cfd_wave_lsrk_workspace(cfd_blocks_t blocks, cfd_precision prec, int n_iter, size_t *bytes);
+
+/*
+ * One step of the 2S method above for the wave system of cfd_wave_rk_step
+ * with Kreiss-Oliger dissipation (Eq. dissdef) added to the right-hand side of
+ * both fields in each direction:
+ *     F_Phi = K + sum_i Q_i[Phi],  F_K = sum_i D2_i Phi + sum_i Q_i[K],
+ *     Q_i = -((-1)^r / 2^{2r}) sigma dx_i^{2r-1} (D_+)^r (D_-)^r along axis i.
+ *   sigma >= 0; ko_r = r, 1 <= r <= ng (the stencil of (2r)E_r, Tab. diss_scheme,
+ *   reads r ghosts; the ghosts of both fields are exchanged every stage when
+ *   sigma > 0).  The dissipation sums run in FP64 for CFD_FP64_BANDED and in
+ *   FP32 (added to the FP64 right-hand side) for the tensor-core precisions.
+ * `phi`, `K`: single-field buffers in the field layout, advanced in place.
+ * Errors: CFD_ERR_ARG (bad coefficients, sigma < 0, r out of range, workspace),
+ * CFD_ERR_UNSUPPORTED (FP32 fields, -1 neighbours), CFD_ERR_CUDA.
+ */
+cfd_status cfd_wave_lsrk_step(cfd_blocks_t blocks, void *phi, void *K, double dt, const cfd_lsrk_desc *rk,
+                              double sigma, int ko_r, cfd_precision prec, int n_iter, void *work,
+                              size_t work_bytes, void *stream);
+
 /* Wait for `stream`, then read and clear the device status word of the
  * handle: CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_DEVICE_ASSERT. */
 cfd_status cfd_sync_status(cfd_blocks_t blocks, void *stream);

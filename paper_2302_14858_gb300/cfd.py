@@ -40,7 +40,8 @@ CFD_OP_ALL = 0x1FF
 
 EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd_blocks_bind",
            "cfd_blocks_destroy", "cfd_exchange_ghosts", "cfd_apply_workspace", "cfd_apply",
-           "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_sync_status", "cfd_last_error",
+           "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_wave_lsrk_workspace", "cfd_wave_lsrk_step",
+           "cfd_sync_status", "cfd_last_error",
            "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static")
 KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4}
 
@@ -79,6 +80,18 @@ _lib.cfd_wave_workspace.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
 _lib.cfd_wave_workspace.restype = c_int
 _lib.cfd_wave_rk_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, c_size_t, c_void_p]
 _lib.cfd_wave_rk_step.restype = c_int
+
+
+class LsrkDesc(ctypes.Structure):
+    _fields_ = [("stages", c_int), ("gamma1", POINTER(c_double)), ("gamma2", POINTER(c_double)),
+                ("beta", POINTER(c_double)), ("delta", POINTER(c_double))]
+
+
+_lib.cfd_wave_lsrk_workspace.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
+_lib.cfd_wave_lsrk_workspace.restype = c_int
+_lib.cfd_wave_lsrk_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(LsrkDesc), c_double, c_int,
+                                    c_int, c_int, c_void_p, c_size_t, c_void_p]
+_lib.cfd_wave_lsrk_step.restype = c_int
 _lib.cfd_sync_status.argtypes = [c_void_p, c_void_p]
 _lib.cfd_sync_status.restype = c_int
 _lib.cfd_kernel_launches.argtypes = []
@@ -225,6 +238,26 @@ def cfd_wave_rk_step(blocks: Blocks, phi, K, dt: float, prec: int, n_iter: int, 
     nbytes = work.numel() * work.element_size()
     _check(_lib.cfd_wave_rk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), prec, n_iter, _ptr(work), nbytes,
                                  _stream(stream)))
+
+
+def cfd_wave_lsrk_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
+    n = c_size_t()
+    _check(_lib.cfd_wave_lsrk_workspace(blocks.handle, prec, n_iter, ctypes.byref(n)))
+    return n.value
+
+
+def cfd_wave_lsrk_step(blocks: Blocks, phi, K, dt: float, coef, sigma: float, ko_r: int, prec: int, n_iter: int,
+                       work, stream=None):
+    """coef = (gamma1, gamma2, beta, delta), sequences of equal length (the 2S coefficients)."""
+    g1, g2, be, de = (list(map(float, c)) for c in coef)
+    m = len(be)
+    if not (len(g1) == len(g2) == len(de) == m):
+        raise ValueError("the four coefficient sequences need the same length")
+    arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
+    desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
+    nbytes = work.numel() * work.element_size()
+    _check(_lib.cfd_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), ctypes.byref(desc), float(sigma),
+                                   int(ko_r), prec, n_iter, _ptr(work), nbytes, _stream(stream)))
 
 
 def cfd_sync_status(blocks: Blocks, stream=None):

@@ -326,3 +326,62 @@ def test_pade_family_both_paths(lib, torch, fam, n_iter):
             want = ref[op].reshape(mesh.nblocks, N, N, N)
             assert rel_max(fp[:, q, i], want) < 1e-12, (fam, q, op)
             assert rel_max(tc[:, q, i], want) < TOL_EXACT64, (fam, q, op)
+
+
+@pytest.mark.parametrize("prec,NM,N,n_iter", [(0, 32, 8, 0), (0, 32, 8, 1), (2, 64, 16, 0), (2, 64, 16, 1)])
+def test_wave_lsrk_with_ko_dissipation(lib, torch, prec, NM, N, n_iter):
+    """2S low-storage RK with Kreiss-Oliger dissipation (r = 4, sigma = 0.04) vs the oracle, 3 steps."""
+    from oracle import timestep as T
+    g, sigma, r = 4, 0.04, 4
+    pw = W.plane_waves(17, 4, 10.0)
+    dx = 2 * np.pi / NM
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    # a short-wavelength part makes the dissipation visible
+    phi0 = pw.phi_at(0.0, X, Y, Z) + 0.05 * np.cos(11 * X - 9 * Y + 7 * Z)
+    K0 = pw.K_at(0.0, X, Y, Z)
+    mesh = W.uniform_mesh(NM, N, g)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    E = N + 2 * g
+    tp = torch.from_numpy(C.ghost_fill_3d(phi0, N, g).reshape(-1).copy()).cuda()
+    tk = torch.from_numpy(C.ghost_fill_3d(K0, N, g).reshape(-1).copy()).cuda()
+    work = torch.empty(lib.cfd_wave_lsrk_workspace(B, prec, n_iter), dtype=torch.uint8, device="cuda")
+    coef = T.lsrk2s_rk4_float()
+    dt = 0.25 * dx
+    s2 = oracle_sch("Q13_1_d2")
+    p, k = phi0, K0
+    for _ in range(3):
+        lib.cfd_wave_lsrk_step(B, tp, tk, dt, coef, sigma, r, prec, n_iter, work)
+        p, k = T.wave_lsrk_step(p, k, dt, coef, s2, (dx, dx, dx), N, g, n_iter, sigma, r)
+    lib.cfd_sync_status(B)
+    nb = NM // N
+    gp = tp.cpu().numpy().reshape(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
+    gk = tk.cpu().numpy().reshape(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
+    gp = C.blocks_to_global(gp.reshape(nb, nb, nb, N, N, N))
+    gk = C.blocks_to_global(gk.reshape(nb, nb, nb, N, N, N))
+    tol = 1e-12 if prec == 0 else TOL_EXACT64
+    print("lsrk+ko rel err", rel_max(gp, p), rel_max(gk, k))
+    assert rel_max(gp, p) < tol
+    assert rel_max(gk, k) < tol
+    # without dissipation the oracle's result differs well beyond the tolerance
+    p0, _ = T.wave_lsrk_step(phi0, K0, dt, coef, s2, (dx, dx, dx), N, g, n_iter, 0.0, r)
+    p1, _ = T.wave_lsrk_step(phi0, K0, dt, coef, s2, (dx, dx, dx), N, g, n_iter, sigma, r)
+    assert rel_max(p0, p1) > 10 * tol
+
+
+def test_wave_lsrk_rejects_bad_arguments(lib, torch):
+    NM, N, g = 32, 16, 4
+    mesh = W.uniform_mesh(NM, N, g)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    E = N + 2 * g
+    t = torch.zeros(mesh.nblocks * E ** 3, dtype=torch.float64, device="cuda")
+    work = torch.empty(lib.cfd_wave_lsrk_workspace(B, 0, 0), dtype=torch.uint8, device="cuda")
+    good = ([0.0, 0.5], [1.0, 0.5], [0.5, 1.0], [1.0, 1.0])
+    for sigma, r in [(-0.1, 4), (0.04, 0), (0.04, 5)]:
+        with pytest.raises(lib.CfdError) as e:
+            lib.cfd_wave_lsrk_step(B, t, t.clone(), 0.01, good, sigma, r, 0, 0, work)
+        assert e.value.status == lib.CFD_ERR_ARG
+    with pytest.raises(ValueError):
+        lib.cfd_wave_lsrk_step(B, t, t.clone(), 0.01, ([0.0], [1.0, 0.5], [0.5], [1.0]), 0.0, 4, 0, 0, work)
