@@ -358,6 +358,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--graph", action="store_true", help="also time the step replayed from a captured CUDA graph")
+    ap.add_argument("--integrator", default="erk4", choices=["erk4", "lsrk2s"],
+                    help="wave workload: classical RK4, or the 2S low-storage RK with Kreiss-Oliger dissipation")
+    ap.add_argument("--sigma", type=float, default=0.04, help="Kreiss-Oliger strength for --integrator lsrk2s")
+    ap.add_argument("--ko-r", type=int, default=4, help="Kreiss-Oliger order 2r for --integrator lsrk2s")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -610,21 +614,34 @@ def run_wave(args, spec):
     stream = torch.cuda.current_stream(dev)
     phi, K = phi0.clone(), K0.clone()
 
+    lsrk = args.integrator == "lsrk2s"
+    if lsrk:
+        # a 4-stage 4th-order member of the 2S family (coefficients solved from the order conditions)
+        coef = ([0.0, 0.068841064670197562, 0.62754761399692844, -0.59911219706265022],
+                [1.0, 0.81058824734452378, 1.3891900984667538, 1.2610225117075399],
+                [1.2299693289723146, 0.079894519849001553, 0.93225854169045408, 0.45482163406909008],
+                [1.0, 0.14874467817694941, -0.88063710498437737, 1.0])
+
+    def one_step(prec, work):
+        if lsrk:
+            cfd.cfd_wave_lsrk_step(blocks, phi, K, dt, coef, args.sigma, args.ko_r, prec, spec["n_iter"], work, stream)
+        else:
+            cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream)
+
     def run(prec, steps, timed_region):
-        ws = cfd.cfd_wave_workspace(blocks, prec, spec["n_iter"])
+        ws = (cfd.cfd_wave_lsrk_workspace if lsrk else cfd.cfd_wave_workspace)(blocks, prec, spec["n_iter"])
         work = torch.empty(ws, dtype=torch.uint8, device=dev)
         phi.copy_(phi0)
         K.copy_(K0)
         for _ in range(args.warmup):
-            cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream)
+            one_step(prec, work)
         phi.copy_(phi0)
         K.copy_(K0)
         torch.cuda.synchronize()
-        ms = timed(lambda: cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream),
-                   steps, stream, torch) if timed_region else None
+        ms = timed(lambda: one_step(prec, work), steps, stream, torch) if timed_region else None
         if not timed_region:
             for _ in range(steps):
-                cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream)
+                one_step(prec, work)
             torch.cuda.synchronize()
         cfd.cfd_sync_status(blocks, stream)
         return ms, mode_errors(steps * dt)
@@ -674,6 +691,8 @@ def run_wave(args, spec):
             "data": "synthetic (seeded plane waves)",
             "config": {"workload": args.workload, "path": args.prec, "n_iter": spec["n_iter"], "blocks": mesh.nblocks,
                        "dt_over_dx": 0.25, "modes": spec["modes"], "kmax": spec["kmax"],
+                       "integrator": args.integrator,
+                       "ko": {"sigma": args.sigma, "r": args.ko_r} if lsrk else None,
                        "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
             "steps_per_s": round(1e3 / ms * world, 3), "t_final": args.steps * dt, **err,
             "compare": compare, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
