@@ -52,6 +52,12 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 
+# DRAM traffic of the dominant kernel per launch, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum).  The 256^3 workload exceeds the capture-size rule, so the same kernel
+# was captured on 128^3 with the same 32^3 blocks (one step = 6 launches, 1051.2 MB) and scaled
+# by the 8x points: 8409.6 MB per step / 6 launches.  profiles/k_dense_tc_exact_cfd128_b32_f4.md
+MEASURED_TRAFFIC = {("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1401.6e6}
+
 
 def scheme_descs():
     """Tuned (Q^1_3[eta_c=1], Tabs. num_deg_one/two) interior schemes as the paper prints them.
@@ -472,7 +478,8 @@ def main():
                 "algorithmic_bytes_per_point_op": round(elem * (1 + nops) / nops, 3),
                 "tensor_tflops": round(tcf, 1),
                 "tensor_frac_of_bf16_peak": round(tcf / float(peaks.get("bf16_tflops", 1900.0)), 4),
-                "traffic": None}
+                "traffic": MEASURED_TRAFFIC.get((args.workload, args.prec, n_iter)),
+                "algorithmic_bytes_per_launch": round(algorithmic_bytes(nint, nf, nops, elem) / max(nl / prof_steps, 1))}
     roof.update({"launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
                  "share_of_step": round(tl / ms_total, 4), "events_region": {"steps": prof_steps,
                                                                           "ms_per_step": round(ms_prof, 5)}})
