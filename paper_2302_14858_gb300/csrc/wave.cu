@@ -111,6 +111,86 @@ __global__ void k_wave_rhs(const RhsArgs A) {
   L[n3 + i] = fp;
 }
 
+// The same right-hand side for N in {16, 32} and r = RR, tiled: a CTA of N x TY threads owns
+// TY rows of one block and marches along z.  The x and y stencil taps come from the current z
+// plane staged in shared memory (with an RR-wide halo), the z taps from a queue of 2RR+1 values
+// per thread in registers, so every field value is read from global memory about once per
+// plane instead of 2r+1 times per direction, and converted to the stencil precision TK once (a
+// double-to-float conversion runs on the FP64 pipe).  In FP64 the arithmetic and its order are
+// those of k_wave_rhs (taps m = -r..r summed per axis, axes x, y, z added in that order); in
+// FP32 the weighted directions are also summed in FP32 before the one FP64 add per field.
+template <int N, typename TK, int RR>
+__global__ void __launch_bounds__(256) k_wave_rhs_tiled(const RhsArgs A) {
+  constexpr int TY = 256 / N, W = N + 2 * RR, H = TY + 2 * RR, Q = 2 * RR + 1;
+  __shared__ TK sp_[H][W], sk_[H][W];
+  const int g = A.g, E = N + 2 * g;
+  const long long E2 = (long long)E * E;
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * N + tx;
+  const int y0 = blockIdx.x * TY;
+  const int b = A.blocks[blockIdx.y];
+  const int n3 = N * N * N;
+  const double *phi = A.phi + A.extpre[b], *K = A.K + A.extpre[b];
+  double *L = A.lap + 3 * A.intpre[b];
+  const double wx = __dmul_rn(A.ko, A.scale[(b * 2 + 0) * 3 + 0]);
+  const double wy = __dmul_rn(A.ko, A.scale[(b * 2 + 0) * 3 + 1]);
+  const double wz = __dmul_rn(A.ko, A.scale[(b * 2 + 0) * 3 + 2]);
+  TK c[Q];
+#pragma unroll
+  for (int m = 0; m < Q; ++m) c[m] = (TK)A.c[m];
+  // this thread's column (x, y) in the ghost-extended block
+  const long long col = (long long)(y0 + ty + g) * E + (tx + g);
+  TK qp[Q], qk[Q];
+#pragma unroll
+  for (int m = 0; m < Q - 1; ++m) {  // z = -RR .. RR-1 (ghost planes exist: RR <= g)
+    qp[m + 1] = (TK)phi[(long long)(g + m - RR) * E2 + col];
+    qk[m + 1] = (TK)K[(long long)(g + m - RR) * E2 + col];
+  }
+  for (int z = 0; z < N; ++z) {
+    // shift the z queue and load plane z + RR
+#pragma unroll
+    for (int m = 0; m < Q - 1; ++m) { qp[m] = qp[m + 1]; qk[m] = qk[m + 1]; }
+    qp[Q - 1] = (TK)phi[(long long)(g + z + RR) * E2 + col];
+    qk[Q - 1] = (TK)K[(long long)(g + z + RR) * E2 + col];
+    __syncthreads();  // the previous plane's taps are read
+    const long long plane = (long long)(g + z) * E2;
+    for (int i = t; i < H * W; i += 256) {
+      const int r = i / W, xx = i - r * W;
+      const long long o = plane + (long long)(y0 + r - RR + g) * E + (xx - RR + g);
+      sp_[r][xx] = (TK)phi[o];
+      sk_[r][xx] = (TK)K[o];
+    }
+    __syncthreads();
+    const int i = (z * N + (y0 + ty)) * N + tx;
+    double fk = __dadd_rn(__dadd_rn(L[i], L[n3 + i]), L[2 * n3 + i]);
+    double fp = K[plane + col];
+    TK px = 0, kx = 0, py = 0, ky = 0, pz = 0, kz = 0;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      px += c[m] * sp_[ty + RR][tx + m];
+      kx += c[m] * sk_[ty + RR][tx + m];
+      py += c[m] * sp_[ty + m][tx + RR];
+      ky += c[m] * sk_[ty + m][tx + RR];
+      pz += c[m] * qp[m];
+      kz += c[m] * qk[m];
+    }
+    if constexpr (sizeof(TK) == 8) {
+      fp = __dadd_rn(fp, __dmul_rn(wx, px));
+      fk = __dadd_rn(fk, __dmul_rn(wx, kx));
+      fp = __dadd_rn(fp, __dmul_rn(wy, py));
+      fk = __dadd_rn(fk, __dmul_rn(wy, ky));
+      fp = __dadd_rn(fp, __dmul_rn(wz, pz));
+      fk = __dadd_rn(fk, __dmul_rn(wz, kz));
+    } else {
+      // FP32 stencil precision: the three directions are combined in FP32 too, so that one
+      // conversion and one FP64 add per field remain on the FP64 pipe
+      fp = __dadd_rn(fp, (double)((TK)wx * px + (TK)wy * py + (TK)wz * pz));
+      fk = __dadd_rn(fk, (double)((TK)wx * kx + (TK)wy * ky + (TK)wz * kz));
+    }
+    L[i] = fk;
+    L[n3 + i] = fp;
+  }
+}
+
 struct UpdArgs {
   double *phi, *K;           // field layout: S1, updated in place (interior)
   double *s2p, *s2k;         // interior: S2
@@ -302,7 +382,17 @@ extern "C" cfd_status cfd_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, dou
       A.blocks = B->d_groups[gi];
       A.N = N;
       launch_begin(KF_RK, st);
-      if (N == 32) launch1(std::integral_constant<int, 32>(), A, grid);
+      if (ko_on && ko_r == 4 && (N == 32 || N == 16)) {
+        const dim3 tg((unsigned)(N / (256 / N)), (unsigned)B->groups[gi].size());
+        const dim3 tb((unsigned)N, (unsigned)(256 / N));
+        if (N == 32) {
+          if (prec == CFD_FP64_BANDED) k_wave_rhs_tiled<32, double, 4><<<tg, tb, 0, st>>>(A);
+          else k_wave_rhs_tiled<32, float, 4><<<tg, tb, 0, st>>>(A);
+        } else {
+          if (prec == CFD_FP64_BANDED) k_wave_rhs_tiled<16, double, 4><<<tg, tb, 0, st>>>(A);
+          else k_wave_rhs_tiled<16, float, 4><<<tg, tb, 0, st>>>(A);
+        }
+      } else if (N == 32) launch1(std::integral_constant<int, 32>(), A, grid);
       else if (N == 16) launch1(std::integral_constant<int, 16>(), A, grid);
       else launch1(std::integral_constant<int, 0>(), A, grid);
       launch_end(KF_RK, st);
