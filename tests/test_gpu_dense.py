@@ -385,3 +385,61 @@ def test_wave_lsrk_rejects_bad_arguments(lib, torch):
         assert e.value.status == lib.CFD_ERR_ARG
     with pytest.raises(ValueError):
         lib.cfd_wave_lsrk_step(B, t, t.clone(), 0.01, ([0.0], [1.0, 0.5], [0.5], [1.0]), 0.0, 4, 0, 0, work)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_many_iterations_reach_the_global_scheme(lib, torch, prec):
+    """Eq. iter_center_P iterated to convergence: the decomposed result becomes the undecomposed
+    periodic (global) scheme, on both GPU paths (d_x and d_yy of a sine field, 8^3 blocks of 16^3)."""
+    NM, N, g, n_iter = 128, 16, 4, 14
+    r = W.rng(808)
+    f = W.sine_sum(r, 8, 1, 12)
+    mesh, dx, exts, buf = uniform(NM, N, g, [f])
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    got = apply(lib, torch, B, buf, 1, lib.op_mask(["dx", "dyy"]), prec, n_iter).reshape(mesh.nblocks, 2, N, N, N)
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    fg = f(X, Y, Z)
+    want_dx = np.moveaxis(C.global_periodic(np.moveaxis(fg, 2, 0), oracle_sch("Q13_1_d1"), dx), 0, 2)
+    want_dyy = np.moveaxis(C.global_periodic(np.moveaxis(fg, 1, 0), oracle_sch("Q13_1_d2"), dx), 0, 1)
+    nb = NM // N
+    gdx = C.blocks_to_global(got[:, 0].reshape(nb, nb, nb, N, N, N))
+    gdyy = C.blocks_to_global(got[:, 1].reshape(nb, nb, nb, N, N, N))
+    tol = 1e-10 if prec == 0 else TOL_EXACT64
+    print("iterated to the global scheme", rel_max(gdx, want_dx), rel_max(gdyy, want_dyy))
+    assert rel_max(gdx, want_dx) < tol
+    assert rel_max(gdyy, want_dyy) < tol
+
+
+def test_tensor_cores_reject_unsupported_block_size(lib, torch):
+    """The dense operators are built for N = 16 and 32 only: N = 8 blocks are refused, not computed."""
+    NM, N, g = 32, 8, 4
+    mesh = W.uniform_mesh(NM, N, g)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    buf = np.zeros(mesh.nblocks * (N + 2 * g) ** 3)
+    with pytest.raises(lib.CfdError) as e:
+        apply(lib, torch, B, buf, 1, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT)
+    assert e.value.status == lib.CFD_ERR_UNSUPPORTED
+
+
+def test_exact_slices_fp32_uniform_with_iteration(lib, torch):
+    """FP32 fields on the uniform decomposition with one hybrid iteration (TMA staging for the
+    first halo pass, cp.async with halo columns for the final pass)."""
+    NM, N, g = 64, 16, 4
+    r = W.rng(909)
+    fs = [W.sine_sum(r, 8, 1, 12), W.gaussian(r, 0.1)]
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F32)
+    got = apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 1,
+                dtype=np.float32).reshape(mesh.nblocks, 2, 9, N, N, N)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = 0.0
+    for q in range(2):
+        ref = C.apply_uniform(exts[q].astype(np.float32).astype(np.float64), s1, s2, (dx, dx, dx), N, g, OPS, 1)
+        for i, op in enumerate(OPS):
+            worst = max(worst, rel_max(got[:, q, i], ref[op].reshape(mesh.nblocks, N, N, N)))
+    print("fp32 iterated max rel err", worst)
+    assert worst < TOL_EXACT32
