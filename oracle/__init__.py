@@ -22,6 +22,15 @@ cfd       The block operator: ghost fill (matrix G, Eq. example_G), closed
           iter_scheme), 3D application with symmetrised mixed derivatives
           (Sec. "Z4c: system description"), and classical RK4 for the linear
           wave system.
+timestep  Kreiss-Oliger dissipation (Eq. dissdef) and the two-register (2S)
+          low-storage Runge-Kutta recurrence with its 4-stage 4th-order
+          coefficients.
+biased    Biased first-degree schemes: UCD slow/fast U_M, V_M (Eq.
+          defChenSchemes), their xi closures (Eqs. ucd_slow_closure_chi,
+          ucd_fast_closure_chi), CCU X_M (Eq. LCslowfast), the mirror rule, the
+          bidiagonal block systems (Eq. closure_left_X and its right-biased
+          counterpart), their iteration (Eq. iter_left_X) and the upwinded
+          shift-advection term (Eq. biasderapproxadv).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
 the 3D mixed-derivative path with hybrid iteration (``apply3d`` with

@@ -19,6 +19,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
+from oracle import biased as BI  # noqa: E402
 from oracle import schemes as S  # noqa: E402
 
 
@@ -50,7 +51,21 @@ def build() -> dict:
             q = S.tuned_Q(d, eta_c)
             c = S.centered_closure(q, 6, 4, "mp")
             out[f"Q13_{name}_d{d}"] = _entry(q, c, d, 6, "mp", tab, float(eta_c))
+    # left-biased first-degree schemes with their single-point closures at k*_-
+    # (Tab. ccux_deg_one_col: X_M^- with weight sigma; Tab. num_deg_one: Q^{1,0}_{3,4})
+    from fractions import Fraction
+    for M, sig in ((1, Fraction(37, 100)), (2, Fraction(86, 100)), (3, Fraction(146, 100))):
+        X, xi, Xb = BI.ccu_x(M, sig)
+        out[f"X{M}_d1"] = _biased_entry(X, Xb, 2 * M + 2, 1, "Tab. ccux_deg_one_col")
+    q, qc = BI.tuned_Q1034(mp.mpf(1))
+    out["Q1034_1_d1"] = _biased_entry(q, qc, 6, 2, "Tab. num_deg_one (closure: the mirrored Q^{0,1}_{4,3})")
     return out
+
+
+def _biased_entry(interior, closure, order, kc, cite):
+    b = BI.to_biased(interior, closure, kc)
+    return {"d": 1, "order": order, "biased": True, "a": b.a, "lo": b.lo, "rhs": list(b.rhs),
+            "c_sup": b.c_sup, "c_lo": b.c_lo, "closure": list(b.closure), "kc": kc, "cite": cite}
 
 
 if __name__ == "__main__":
