@@ -256,6 +256,82 @@ cfd_status cfd_wave_lsrk_step(cfd_blocks_t blocks, void *phi, void *K, double dt
                               double sigma, int ko_r, cfd_precision prec, int n_iter, void *work,
                               size_t work_bytes, void *stream);
 
+/*
+ * Biased (upwind) first-degree compact scheme, Eq. defChenSchemes with a
+ * two-point left side (Sec. "Domain decomposition: dispersion relation
+ * preservation"), given in its left-biased form S_+ (Im eta~ <= 0; e.g. the
+ * CCU schemes X_M^- of Tab. ccux_deg_one_col or Q^{1,0}_{3,4} of
+ * Tab. num_deg_one).  On a block (local k = 0..N-1, k*_- = 0, k*_+ = N-1):
+ *   interior rows k = 1..N-1 (Eq. closure_left_X):
+ *     a d_{k-1} + d_k = dx^{-1} sum_{i<rhs_n} rhs[i] f_{k + rhs_lo + i}
+ *   closure row k = k*_-:
+ *     d_k + closure_sup d_{k+1} = dx^{-1} sum_{i<closure_n} closure[i] f_{k + closure_lo + i}
+ * The right-biased scheme S_- is its mirror (the rule stated with
+ * Tabs. ucd_slow and ccux_deg_one_col): alpha^{(1)}_m -> alpha^{(1)}_{-m},
+ * alpha^{(0)}_m -> -alpha^{(0)}_{-m}, closed at k*_+.  Hybrid iteration
+ * (Eq. iter_left_X) fixes the derivative at k^c_- = k*_- - kc (S_-:
+ * k^c_+ = k*_+ + kc) to the neighbour's previous iterate and solves the
+ * interior rows from there.
+ *   order        formal order (informational, >= 1).
+ *   a            alpha^{(1)}_{-1}, |a| < 1 (the bidiagonal solve then damps
+ *                rounding); closure_sup with |closure_sup * a| < 1.
+ *   rhs_lo/rhs_n, closure_lo/closure_n   offsets and lengths (<= 12 taps,
+ *                offsets within -6..6); host arrays read during the call.
+ *   kc           1, 2 or 3.
+ * Stencil support of this build: ng = 4 with the interior offsets within
+ * -4..4 and the closure's within -4..5 (Tab. ccux M = 1, 2; Q^{1,0}_{3,4}),
+ * or ng = 6 with -5..5 and -5..6 (M = 3).
+ */
+typedef struct cfd_biased_desc {
+  int order;
+  double a;
+  int rhs_lo, rhs_n;
+  const double *rhs;
+  double closure_sup;
+  int closure_lo, closure_n;
+  const double *closure;
+  int kc;
+} cfd_biased_desc;
+
+/* Attach the biased scheme to a scheme handle (before cfd_blocks_bind, which
+ * builds its per-block-size tables).  Errors: CFD_ERR_ARG. */
+cfd_status cfd_scheme_set_biased(cfd_scheme_t scheme, const cfd_biased_desc *desc);
+
+/* Device workspace of cfd_apply_biased / cfd_advect (bytes; 0 without iteration). */
+cfd_status cfd_biased_workspace(cfd_blocks_t blocks, int nfields, int n_iter, size_t *bytes);
+
+/*
+ * Biased first derivatives of ghost-filled fields: for every block, field
+ * and axis in `axis_mask` (CFD_OP_DX | CFD_OP_DY | CFD_OP_DZ), D_i[S_+] f
+ * (side = +1) or D_i[S_-] f (side = -1), solved per pencil in FP64 as the
+ * bidiagonal block system above (n_iter = 0) or its iteration (n_iter > 0,
+ * Jacobi: every block reads its neighbours' iterate i-1).  An axis along
+ * which a block is its own neighbour on both faces uses the undecomposed
+ * cyclic scheme.  Output layout as cfd_apply (axes in bit order).
+ *   prec   CFD_FP64_BANDED (the only arithmetic of this path).
+ * Errors: CFD_ERR_ARG (no biased scheme bound, bad mask/side, workspace),
+ * CFD_ERR_UNSUPPORTED (stencil support, iteration without face neighbours,
+ * other precisions), CFD_ERR_CUDA.
+ */
+cfd_status cfd_apply_biased(cfd_blocks_t blocks, const void *fields, int nfields, unsigned axis_mask, int side,
+                            cfd_precision prec, int n_iter, void *out, void *work, size_t work_bytes,
+                            void *stream);
+
+/*
+ * Upwinded shift advection (Eq. biasderapproxadv with the advection speed
+ * replaced by the pointwise shift, Sec. "Z4c: system description"): for every
+ * block and field
+ *     out = sum_{i = x, y, z} beta^i_+ D_i[S_+] f + beta^i_- D_i[S_-] f,
+ *     beta_+- = (beta +- |beta|) / 2,
+ * i.e. beta^i d_i f with the left-biased scheme where beta^i > 0 and the
+ * right-biased one where beta^i < 0.  `beta` holds three fields (beta^x,
+ * beta^y, beta^z) in the field layout (ghosts unused); `out` one N^3 array
+ * per block and field.  Arithmetic as cfd_apply_biased; the three axis terms
+ * are added in the order x, y, z.
+ */
+cfd_status cfd_advect(cfd_blocks_t blocks, const void *fields, int nfields, const void *beta, cfd_precision prec,
+                      int n_iter, void *out, void *work, size_t work_bytes, void *stream);
+
 /* Wait for `stream`, then read and clear the device status word of the
  * handle: CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_DEVICE_ASSERT. */
 cfd_status cfd_sync_status(cfd_blocks_t blocks, void *stream);
@@ -266,7 +342,8 @@ const char *cfd_last_error(void);
 /*
  * Diagnostics (no counterpart in the paper).  Kernel families:
  * 0 ghost exchange, 1 banded line solve, 2 RK4 combine, 3 dense tensor-core
- * operator, 4 dense halo rows.  cfd_kernel_launches() counts every kernel the
+ * operator, 4 dense halo rows, 5 biased line solve (cfd_apply_biased,
+ * cfd_advect).  cfd_kernel_launches() counts every kernel the
  * library has launched in this process.  With profiling on, every launch is
  * bracketed by CUDA events recorded on its own stream; cfd_profile_read()
  * (after the stream has finished) returns the number of launches and their

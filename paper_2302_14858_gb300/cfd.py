@@ -42,8 +42,9 @@ EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd
            "cfd_blocks_destroy", "cfd_exchange_ghosts", "cfd_apply_workspace", "cfd_apply",
            "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_wave_lsrk_workspace", "cfd_wave_lsrk_step",
            "cfd_sync_status", "cfd_last_error",
-           "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static")
-KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4}
+           "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static",
+           "cfd_scheme_set_biased", "cfd_biased_workspace", "cfd_apply_biased", "cfd_advect")
+KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4, "biased": 5}
 
 
 class CfdError(RuntimeError):
@@ -92,6 +93,24 @@ _lib.cfd_wave_lsrk_workspace.restype = c_int
 _lib.cfd_wave_lsrk_step.argtypes = [c_void_p, c_void_p, c_void_p, c_double, POINTER(LsrkDesc), c_double, c_int,
                                     c_int, c_int, c_void_p, c_size_t, c_void_p]
 _lib.cfd_wave_lsrk_step.restype = c_int
+
+
+class BiasedDesc(ctypes.Structure):
+    _fields_ = [("order", c_int), ("a", c_double), ("rhs_lo", c_int), ("rhs_n", c_int), ("rhs", POINTER(c_double)),
+                ("closure_sup", c_double), ("closure_lo", c_int), ("closure_n", c_int),
+                ("closure", POINTER(c_double)), ("kc", c_int)]
+
+
+_lib.cfd_scheme_set_biased.argtypes = [c_void_p, POINTER(BiasedDesc)]
+_lib.cfd_scheme_set_biased.restype = c_int
+_lib.cfd_biased_workspace.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
+_lib.cfd_biased_workspace.restype = c_int
+_lib.cfd_apply_biased.argtypes = [c_void_p, c_void_p, c_int, c_uint, c_int, c_int, c_int, c_void_p, c_void_p,
+                                  c_size_t, c_void_p]
+_lib.cfd_apply_biased.restype = c_int
+_lib.cfd_advect.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_size_t,
+                            c_void_p]
+_lib.cfd_advect.restype = c_int
 _lib.cfd_sync_status.argtypes = [c_void_p, c_void_p]
 _lib.cfd_sync_status.restype = c_int
 _lib.cfd_kernel_launches.argtypes = []
@@ -258,6 +277,39 @@ def cfd_wave_lsrk_step(blocks: Blocks, phi, K, dt: float, coef, sigma: float, ko
     nbytes = work.numel() * work.element_size()
     _check(_lib.cfd_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), ctypes.byref(desc), float(sigma),
                                    int(ko_r), prec, n_iter, _ptr(work), nbytes, _stream(stream)))
+
+
+def cfd_scheme_set_biased(scheme: Scheme, d: dict):
+    """Attach a left-biased scheme: dict {order, a, lo, rhs, c_sup, c_lo, closure, kc}
+    (a = alpha^{(1)}_{-1}, rhs over offsets lo.., closure over offsets c_lo.. with
+    alpha-bar^{(1)}_{+1} = c_sup)."""
+    rhs = (c_double * len(d["rhs"]))(*map(float, d["rhs"]))
+    clo = (c_double * len(d["closure"]))(*map(float, d["closure"]))
+    desc = BiasedDesc(int(d["order"]), float(d["a"]), int(d["lo"]), len(d["rhs"]), ctypes.cast(rhs, POINTER(c_double)),
+                      float(d["c_sup"]), int(d["c_lo"]), len(d["closure"]), ctypes.cast(clo, POINTER(c_double)),
+                      int(d["kc"]))
+    _check(_lib.cfd_scheme_set_biased(scheme.handle, ctypes.byref(desc)))
+
+
+def cfd_biased_workspace(blocks: Blocks, nfields: int, n_iter: int) -> int:
+    n = c_size_t()
+    _check(_lib.cfd_biased_workspace(blocks.handle, nfields, n_iter, ctypes.byref(n)))
+    return n.value
+
+
+def _nbytes(work) -> int:
+    return 0 if work is None else work.numel() * work.element_size()
+
+
+def cfd_apply_biased(blocks: Blocks, fields, nfields: int, axis_mask: int, side: int, prec: int, n_iter: int, out,
+                     work=None, stream=None):
+    _check(_lib.cfd_apply_biased(blocks.handle, _ptr(fields), nfields, axis_mask, side, prec, n_iter, _ptr(out),
+                                 _ptr(work), _nbytes(work), _stream(stream)))
+
+
+def cfd_advect(blocks: Blocks, fields, nfields: int, beta, prec: int, n_iter: int, out, work=None, stream=None):
+    _check(_lib.cfd_advect(blocks.handle, _ptr(fields), nfields, _ptr(beta), prec, n_iter, _ptr(out), _ptr(work),
+                           _nbytes(work), _stream(stream)))
 
 
 def cfd_sync_status(blocks: Blocks, stream=None):

@@ -487,6 +487,7 @@ cfd_status cfd_blocks_bind(cfd_scheme_t scheme, int nblocks, const int *block_n,
   if (!B) { set_error("out of host memory"); return CFD_ERR_ALLOC; }
   B->s[0] = scheme->s[0];
   B->s[1] = scheme->s[1];
+  B->biased = scheme->biased;
   cudaGetDevice(&B->device);
   if (cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess) B->num_sms = 0;
   B->nblocks = nblocks;
@@ -542,6 +543,11 @@ cfd_status cfd_blocks_bind(cfd_scheme_t scheme, int nblocks, const int *block_n,
     for (int d = 0; d < 2; ++d)
       if (B->s[d].present) build_tables(B->s[d], kv.first, os.tab[d]);
     B->ops.push_back(os);
+    if (B->biased.present) {
+      BiasedTables bt;
+      build_biased_tables(B->biased, kv.first, bt);
+      B->btab.push_back(bt);
+    }
   }
   // per-block scale 1/dx^d, [b][deg][axis x,y,z]
   std::vector<double> scale((size_t)nblocks * 6);

@@ -26,6 +26,46 @@ struct SchemeCoef {
   double clo[2 * kMaxH + 1] = {};
 };
 
+// Biased first-degree scheme (left-biased form) as given to cfd_scheme_set_biased.
+constexpr int kBOff = 6;                 // coefficient of offset m stored at m + kBOff
+constexpr int kBTaps = 2 * kBOff + 1;    // offsets -6..6
+struct BiasedCoef {
+  bool present = false;
+  int order = 0, lo = 0, hi = 0, clo = 0, chi = 0, kc = 1;  // offset ranges (inclusive)
+  double a = 0.0, csup = 0.0;
+  double rhs[kBTaps] = {}, cl[kBTaps] = {};
+};
+
+// Per block size: what one biased pencil solve needs (passed by value).
+struct BiasedTables {
+  int N, kc;
+  double a, csup;
+  double inv01;            // 1 / (1 - csup a): the 2x2 coupling of the closure row
+  double cyc_inv;          // 1 / (1 - (-a)^N): cyclic (single-block periodic) axis
+  double rhs[kBTaps], clo[kBTaps];
+  double pw[kMaxN + 1];    // (-a)^j
+};
+
+// One biased axis pass over a group of same-size blocks.
+struct BiasedParams {
+  const void *in;          // field buffer (dtype)
+  const void *beta;        // shift fields (advect mode)
+  void *out;
+  const int *blocks;
+  const long long *extpre, *intpre;
+  const int *nbr;
+  const double *scale;     // [nblocks][2][3]; the degree-1 entries are used
+  const double *halo_in;   // [nblocks][nf][N^2][2]: (d+ at N-kc, d- at kc-1) of the previous iterate
+  double *halo_out;
+  int nblk, nf, nops, opidx;
+  int axis, t1, t2;        // box axes (0 z, 1 y, 2 x)
+  int mode;                // 0 d[S+], 1 d[S-], 2 advect (beta_+ d[S+] + beta_- d[S-])
+  int accum;               // 1: add into out
+  int pass, last;
+};
+
+void build_biased_tables(const BiasedCoef &c, int N, BiasedTables &T);
+
 // Everything one pencil solve needs for one (block size N, degree d).
 // Passed to kernels by value.
 struct LineTables {
@@ -81,6 +121,7 @@ struct OpSet {           // device copies per distinct block size
 
 struct cfd_scheme_s {
   cfd::SchemeCoef s[2];
+  cfd::BiasedCoef biased;
 };
 
 struct cfd_blocks_s {
@@ -95,6 +136,8 @@ struct cfd_blocks_s {
   std::vector<int> sizes;              // distinct N, increasing
   std::vector<std::vector<int>> groups;  // block ids per distinct N
   std::vector<cfd::OpSet> ops;         // per distinct N
+  cfd::BiasedCoef biased;
+  std::vector<cfd::BiasedTables> btab; // per distinct N (when biased.present)
   bool iter_ok = true;                 // same-size face neighbours everywhere
   // device copies
   int *d_nbr = nullptr;
@@ -116,7 +159,7 @@ void set_error(const std::string &msg);
 cfd_status cuda_fail(cudaError_t e, const char *what);
 
 // launch accounting (profile.cpp)
-enum KernelFamily { KF_EXCHANGE = 0, KF_LINE = 1, KF_RK = 2, KF_DENSE = 3, KF_HALO = 4, KF_COUNT = 5 };
+enum KernelFamily { KF_EXCHANGE = 0, KF_LINE = 1, KF_RK = 2, KF_DENSE = 3, KF_HALO = 4, KF_BIASED = 5, KF_COUNT = 6 };
 void launch_begin(int family, cudaStream_t st);
 void launch_end(int family, cudaStream_t st);
 

@@ -1,0 +1,223 @@
+"""GPU parity of the biased (upwind) FP64 path through the C ABI against oracle/biased.py.
+
+Biased derivatives (Eq. closure_left_X and its mirror, Eq. iter_left_X), the
+single-block cyclic case, FP32 fields and the upwinded shift-advection term
+(Eq. biasderapproxadv).  Tolerances: FP64 within 1e-12 relative max error per
+(field, axis); FP32 fields within 2e-6 of the oracle's FP64 result on the same
+(rounded) input.
+"""
+import numpy as np
+import pytest
+
+from oracle import biased as B
+from oracle import cfd as C
+from tests.helpers import SCHEMES, desc, rel_max
+from tests.test_gpu_banded import case_fields, uniform_case
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+AXES = ("x", "y", "z")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_14858_gb300 import build
+    build.build()
+    from paper_2302_14858_gb300 import cfd
+    return cfd
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def biased_of(name):
+    e = SCHEMES[name]
+    return B.Biased(e["a"], e["lo"], tuple(e["rhs"]), e["c_sup"], e["c_lo"], tuple(e["closure"]), e["kc"])
+
+
+def bind(lib, name, mesh, g, dtype):
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), None)
+    lib.cfd_scheme_set_biased(s, SCHEMES[name])
+    return lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, dtype)
+
+
+def run_biased(lib, torch, blocks, buf, nf, mask, side, n_iter, dtype=np.float64):
+    dev = torch.device("cuda", 0)
+    fields = torch.from_numpy(np.ascontiguousarray(buf.astype(dtype))).to(dev)
+    nops = bin(mask).count("1")
+    nint = sum(int(n) ** 3 for n in blocks.block_n)
+    out = torch.zeros(nint * nf * nops, dtype=fields.dtype, device=dev)
+    ws = lib.cfd_biased_workspace(blocks, nf, n_iter)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    lib.cfd_apply_biased(blocks, fields, nf, mask, side, lib.CFD_FP64_BANDED, n_iter, out, work)
+    lib.cfd_sync_status(blocks)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check_biased(lib, torch, name, NM, N, g, side, n_iter, nf=2, seed=11):
+    fields = case_fields(seed, nf)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    blocks = bind(lib, name, mesh, g, lib.CFD_F64)
+    got = run_biased(lib, torch, blocks, buf, nf, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, n_iter)
+    got = got.reshape(mesh.nblocks, nf, 3, N, N, N)
+    b = biased_of(name)
+    for q in range(nf):
+        want = B.biased_uniform(exts[q], b, side, (dx, dx, dx), N, g, AXES, n_iter)
+        for i, c in enumerate(AXES):
+            w = want[c].reshape(mesh.nblocks, N, N, N)
+            assert rel_max(got[:, q, i], w) < TOL64, (name, side, n_iter, q, c, rel_max(got[:, q, i], w))
+
+
+@pytest.mark.parametrize("name", ["X1_d1", "X2_d1", "Q1034_1_d1"])
+@pytest.mark.parametrize("side", [1, -1])
+@pytest.mark.parametrize("n_iter", [0, 1, 2])
+def test_biased_parity_16(lib, torch, name, side, n_iter):
+    """64^3 as 4^3 blocks of 16^3, ng = 4: closed block systems and their iteration."""
+    check_biased(lib, torch, name, 64, 16, 4, side, n_iter)
+
+
+@pytest.mark.parametrize("NM,N", [(64, 32), (32, 8)])
+@pytest.mark.parametrize("side", [1, -1])
+def test_biased_parity_other_sizes(lib, torch, NM, N, side):
+    """Block sizes 32 and 8 (several tiles of pencils; 8 leaves half a thread block idle)."""
+    check_biased(lib, torch, "X2_d1", NM, N, 4, side, 1)
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_biased_parity_wide_stencil(lib, torch, side):
+    """X_3 (interior offsets -5..5, closure to 6) with ng = 6."""
+    check_biased(lib, torch, "X3_d1", 64, 16, 6, side, 1)
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_single_block_is_the_cyclic_scheme(lib, torch, side):
+    """A 32^3 block that is its own neighbour: the undecomposed periodic biased scheme."""
+    NM = N = 32
+    g = 4
+    fields = case_fields(5, 1)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    blocks = bind(lib, "Q1034_1_d1", mesh, g, lib.CFD_F64)
+    got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, 2)
+    got = got.reshape(3, N, N, N)
+    b = biased_of("Q1034_1_d1")
+    fg = exts[0][0, 0, 0][g:g + N, g:g + N, g:g + N]
+    for i, ax in enumerate((2, 1, 0)):
+        want = np.moveaxis(B.global_periodic(np.moveaxis(fg, ax, 0), b, side, dx), 0, ax)
+        assert rel_max(got[i], want) < TOL64
+
+
+def test_iteration_reaches_the_global_scheme(lib, torch):
+    """Three iterations of Eq. iter_left_X on 16^3 blocks: the global periodic result."""
+    NM, N, g = 64, 16, 4
+    fields = case_fields(3, 1)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    blocks = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    b = biased_of("X2_d1")
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    fg = fields[0](X, Y, Z)
+    for side in (1, -1):
+        got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX, side, 3).reshape(mesh.nblocks, N, N, N)
+        want = np.moveaxis(B.global_periodic(np.moveaxis(fg, 2, 0), b, side, dx), 0, 2)
+        assert rel_max(C.blocks_to_global(got.reshape(4, 4, 4, N, N, N)), want) < 1e-13
+        got0 = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX, side, 0).reshape(mesh.nblocks, N, N, N)
+        assert rel_max(C.blocks_to_global(got0.reshape(4, 4, 4, N, N, N)), want) > 1e-9
+
+
+def test_float32_fields(lib, torch):
+    NM, N, g = 64, 16, 4
+    fields = case_fields(9, 2)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    buf32 = buf.astype(np.float32)
+    blocks = bind(lib, "X2_d1", mesh, g, lib.CFD_F32)
+    got = run_biased(lib, torch, blocks, buf32, 2, lib.CFD_OP_DX | lib.CFD_OP_DZ, -1, 1, np.float32)
+    got = got.reshape(mesh.nblocks, 2, 2, N, N, N).astype(np.float64)
+    b = biased_of("X2_d1")
+    E = N + 2 * g
+    for q in range(2):
+        ext = buf32.reshape(mesh.nblocks, 2, E, E, E)[:, q].astype(np.float64).reshape(exts[q].shape)
+        want = B.biased_uniform(ext, b, -1, (dx, dx, dx), N, g, ("x", "z"), 1)
+        for i, c in enumerate(("x", "z")):
+            assert rel_max(got[:, q, i], want[c].reshape(mesh.nblocks, N, N, N)) < 2e-6
+
+
+def shift_fields():
+    """Shift components with both signs inside every block."""
+    return [lambda X, Y, Z: np.cos(X + 2 * Z) + 0.1,
+            lambda X, Y, Z: np.sin(Y - X),
+            lambda X, Y, Z: 0.5 * np.cos(3 * Y) * np.sin(Z)]
+
+
+@pytest.mark.parametrize("name,g", [("X2_d1", 4), ("Q1034_1_d1", 4)])
+@pytest.mark.parametrize("n_iter", [0, 1])
+def test_advect_parity(lib, torch, name, g, n_iter):
+    """out = sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f on 4^3 blocks of 16^3, 3 fields."""
+    NM, N, nf = 64, 16, 3
+    fields = case_fields(21, nf)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    _, _, bexts, bbuf = uniform_case(NM, N, g, shift_fields())
+    blocks = bind(lib, name, mesh, g, lib.CFD_F64)
+    dev = torch.device("cuda", 0)
+    f_t = torch.from_numpy(buf).to(dev)
+    b_t = torch.from_numpy(bbuf).to(dev)
+    out = torch.zeros(mesh.nblocks * nf * N ** 3, dtype=torch.float64, device=dev)
+    ws = lib.cfd_biased_workspace(blocks, nf, n_iter)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    lib.cfd_advect(blocks, f_t, nf, b_t, lib.CFD_FP64_BANDED, n_iter, out, work)
+    lib.cfd_sync_status(blocks)
+    got = out.cpu().numpy().reshape(mesh.nblocks, nf, N, N, N)
+    I = slice(g, g + N)
+    beta = [e[:, :, :, I, I, I] for e in bexts]
+    b = biased_of(name)
+    for q in range(nf):
+        want = B.advect_uniform(exts[q], beta, b, (dx, dx, dx), N, g, n_iter).reshape(mesh.nblocks, N, N, N)
+        assert rel_max(got[:, q], want) < TOL64
+
+
+def test_rejections(lib, torch):
+    NM, N, g = 32, 16, 4
+    fields = case_fields(1, 1)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    dev = torch.device("cuda", 0)
+    f_t = torch.from_numpy(buf).to(dev)
+    out = torch.zeros(mesh.nblocks * N ** 3 * 3, dtype=torch.float64, device=dev)
+    # no biased scheme bound
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), None)
+    B0 = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    with pytest.raises(lib.CfdError) as e:
+        lib.cfd_apply_biased(B0, f_t, 1, lib.CFD_OP_DX, 1, 0, 0, out)
+    assert e.value.status == lib.CFD_ERR_ARG
+    blocks = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    with pytest.raises(lib.CfdError) as e:                       # tensor cores: not on this path
+        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 1, lib.CFD_TC_BF16_EXACT, 0, out)
+    assert e.value.status == lib.CFD_ERR_UNSUPPORTED
+    with pytest.raises(lib.CfdError) as e:                       # side must be +-1
+        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 0, 0, 0, out)
+    assert e.value.status == lib.CFD_ERR_ARG
+    with pytest.raises(lib.CfdError) as e:                       # second-degree ops are not biased
+        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DXX, 1, 0, 0, out)
+    assert e.value.status == lib.CFD_ERR_ARG
+    with pytest.raises(lib.CfdError) as e:                       # iteration needs the halo workspace
+        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 1, 0, 1, out, None)
+    assert e.value.status == lib.CFD_ERR_ARG
+    # ghost width outside the compiled windows
+    mesh5 = uniform_case(NM, N, 5, fields)[0]
+    s5 = lib.cfd_scheme_create(desc("Q13_1_d1"), None)
+    lib.cfd_scheme_set_biased(s5, SCHEMES["X2_d1"])
+    B5 = lib.cfd_blocks_bind(s5, mesh5.n, mesh5.dx, mesh5.neighbors, 5, lib.CFD_F64)
+    with pytest.raises(lib.CfdError) as e:
+        lib.cfd_apply_biased(B5, f_t, 1, lib.CFD_OP_DX, 1, 0, 0, out)
+    assert e.value.status == lib.CFD_ERR_UNSUPPORTED
+    # bad descriptors are refused on the host
+    bad = dict(SCHEMES["X2_d1"], a=1.2)
+    with pytest.raises(lib.CfdError):
+        lib.cfd_scheme_set_biased(s5, bad)
+    bad = dict(SCHEMES["X2_d1"], kc=0)
+    with pytest.raises(lib.CfdError):
+        lib.cfd_scheme_set_biased(s5, bad)
+    torch.cuda.synchronize()
