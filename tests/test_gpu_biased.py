@@ -112,7 +112,8 @@ def test_single_block_is_the_cyclic_scheme(lib, torch, side):
 
 
 def test_iteration_reaches_the_global_scheme(lib, torch):
-    """Three iterations of Eq. iter_left_X on 16^3 blocks: the global periodic result."""
+    """Five iterations of Eq. iter_left_X on 16^3 blocks (each one damps the closure error by
+    about |a|^(N+kc) = 1.4e-3): the global periodic result."""
     NM, N, g = 64, 16, 4
     fields = case_fields(3, 1)
     mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
@@ -122,7 +123,7 @@ def test_iteration_reaches_the_global_scheme(lib, torch):
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     fg = fields[0](X, Y, Z)
     for side in (1, -1):
-        got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX, side, 3).reshape(mesh.nblocks, N, N, N)
+        got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX, side, 5).reshape(mesh.nblocks, N, N, N)
         want = np.moveaxis(B.global_periodic(np.moveaxis(fg, 2, 0), b, side, dx), 0, 2)
         assert rel_max(C.blocks_to_global(got.reshape(4, 4, 4, N, N, N)), want) < 1e-13
         got0 = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX, side, 0).reshape(mesh.nblocks, N, N, N)
