@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gpoint-ops/s: split-BF16 TC CFD vs FP64 banded solve, err ≤1e-6 vs FP64"
+ADVECT_METRIC = "Gpoint-ops/s: upwinded shift advection (biased CCU X_2 pencil solves)"
 L2_BYTES = 129 * 2 ** 20
 FP64_NOMINAL_GFLOPS = 1250.0      # GB300 FP64 (non-tensor) nominal, profiling recipe table
 
@@ -49,6 +50,12 @@ WORKLOADS = {
     "box448x16_64x32_f22_fp32": dict(kind="boxinbox", nf=22, fields=4, dtype="f32", n_iter=0),
     # linear wave u_tt = Laplacian u, 256^3 as 512 blocks of 32^3, plane waves |k| <= 20, RK4, dt = 0.25 dx
     "wave256_b32_rk4": dict(kind="wave", NM=256, N=32, nf=2, dtype="f64", n_iter=0, modes=8, kmax=20.0),
+    # upwinded shift advection sum_i beta^i d_i f (Eq. biasderapproxadv) with the CCU X_2^-
+    # scheme and its mirror (Tab. ccux_deg_one_col), 256^3 as 512 blocks of 32^3, 4 FP64 fields,
+    # one iteration of Eq. iter_left_X
+    "advect256_b32_x2_f4_fp64": dict(kind="advect", NM=256, N=32, nf=4, fields=3, dtype="f64", n_iter=1),
+    # the same on 128^3 as 64 blocks of 32^3 (small case for ncu captures)
+    "advect128_b32_x2_f4_fp64": dict(kind="advect", NM=128, N=32, nf=4, fields=3, dtype="f64", n_iter=1),
 }
 DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 
@@ -69,6 +76,33 @@ def scheme_descs():
     d2 = {"deriv": 2, "order": 6, "a": 0.24246603,
           "rhs": [-0.0037062571, 0.14095923, 0.95445144, -2.1834088, 0.95445144, 0.14095923, -0.0037062571]}
     return d1, d2
+
+
+def biased_desc():
+    """CCU X_2^- (weight 86/100) with its closure X-bar_2^-, the exact rationals printed in
+    Tab. ccux_deg_one_col; iteration node k^c_- = k*_- - 1 (Sec. "Domain decomposition:
+    iteration of closures")."""
+    from fractions import Fraction as Fr
+    rhs = ["-43/56000", "1523/126000", "-857/6000", "-39697/36000", "245/288", "2723/6000", "-1459/18000",
+           "2899/252000", "-43/56000"]
+    clo = ["194871521/170360232000", "-242883881/17036023200", "3813668231/42590058000",
+           "-8537761009/18252882000", "-3401756057/4056196000", "40137795113/36505764000",
+           "507715327/3650576400", "-338742841/42590058000", "-458269213/511080696000", "16295059/63885087000"]
+    return {"order": 6, "a": float(Fr(407, 600)), "lo": -4, "rhs": [float(Fr(v)) for v in rhs],
+            "c_sup": float(Fr(407, 600)), "c_lo": -4, "closure": [float(Fr(v)) for v in clo], "kc": 1}
+
+
+def shift_torch(X, Y, Z):
+    """Shift components (beta^x, beta^y, beta^z), both signs inside every block."""
+    import torch
+    return (torch.cos(X + 2 * Z) + 0.1, torch.sin(Y - X), 0.5 * torch.cos(3 * Y) * torch.sin(Z))
+
+
+def advect_flops_per_point_axis(n_taps=9, sides=2):
+    """FP64 flops per point, field and axis of one biased pass: per side the FMA chain over the
+    interior taps (2 n_taps), the 1/dx scale and the recurrence FMA; then the upwind combine
+    (|beta|, two weights, two products, one sum) and the accumulation over axes."""
+    return sides * (2 * n_taps + 1 + 2) + 7
 
 
 # ------------------------------------------------------------------ clocks
@@ -136,7 +170,7 @@ def build_workload(name, dev, torch):
     spec = WORKLOADS[name]
     funcs = W.workload_fields(spec["fields"])[: spec["nf"]]
     tdt = torch.float64 if spec["dtype"] == "f64" else torch.float32
-    if spec["kind"] == "uniform":
+    if spec["kind"] in ("uniform", "advect"):
         NM, N, g = spec["NM"], spec["N"], 4
         mesh = W.uniform_mesh(NM, N, g)
         nb, E = NM // N, N + 2 * g
@@ -256,6 +290,30 @@ def cpu_baseline(spec, seconds=12.0):
         el = time.perf_counter() - t0
         return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
                 "sample": f"oracle wave_rk4_step, {NS}^3 as {(NS // N) ** 3} blocks of {N}^3, {reps} RK4 steps"}
+    if spec["kind"] == "advect":
+        from oracle import biased as BO
+        d = biased_desc()
+        bs = BO.Biased(d["a"], d["lo"], tuple(d["rhs"]), d["c_sup"], d["c_lo"], tuple(d["closure"]), d["kc"])
+        NS, N = 64, spec["N"]
+        f = W.workload_fields(spec["fields"])[0]
+        dx = 2 * np.pi / NS
+        x = (np.arange(NS) + 0.5) * dx
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        ext = C.ghost_fill_3d(f(X, Y, Z), N, g)
+        beta = [C.global_to_blocks(v, N) for v in (np.cos(X + 2 * Z) + 0.1, np.sin(Y - X),
+                                                   0.5 * np.cos(3 * Y) * np.sin(Z))]
+        units, reps = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            BO.advect_uniform(ext, beta, bs, (dx, dx, dx), N, g, spec["n_iter"])
+            units += NS ** 3
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        el = time.perf_counter() - t0
+        return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle advect_uniform, 1 field, {NS}^3 as {(NS // N) ** 3} blocks of {N}^3, "
+                          f"n_iter={spec['n_iter']}, {reps} reps"}
     if spec["kind"] == "uniform":
         NM, N = spec["NM"], spec["N"]
         # sample: one field on a (NM/2)^3 periodic sub-problem with the same block size
@@ -381,6 +439,8 @@ def main():
         return run_reference(args, spec, rank)
     if spec["kind"] == "wave":
         return run_wave(args, spec)
+    if spec["kind"] == "advect":
+        return run_advect(args, spec)
 
     import torch
     if world > 1:
@@ -578,6 +638,137 @@ def main():
         dist.destroy_process_group()
 
 
+def run_advect(args, spec):
+    """Upwinded shift advection: Gpoint-ops/s = interior points x fields (one advective term
+    sum_i beta^i d_i f each) / step time; a step is the ghost exchange of the fields plus
+    cfd_advect (FP64 biased pencil solves, both biases, every axis, with iteration)."""
+    import torch
+    from paper_2302_14858_gb300 import cfd
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    scheme = cfd.cfd_scheme_create(scheme_descs()[0], None)
+    cfd.cfd_scheme_set_biased(scheme, biased_desc())
+    _, mesh, fields = build_workload(args.workload, dev, torch)
+    NM, N, g = spec["NM"], spec["N"], 4
+    nb, E = NM // N, N + 2 * g
+    x = (torch.arange(NM, dtype=torch.float64, device=dev) + 0.5) * (2 * math.pi / NM)
+    Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+    idx = (torch.arange(nb, device=dev)[:, None] * N + torch.arange(-g, N + g, device=dev)[None, :]) % NM
+    beta = torch.empty((mesh.nblocks, 3, E, E, E), dtype=torch.float64, device=dev)
+    for i, bg in enumerate(shift_torch(X, Y, Z)):
+        beta[:, i] = bg[idx[:, None, None, :, None, None], idx[None, :, None, None, :, None],
+                        idx[None, None, :, None, None, :]].reshape(mesh.nblocks, E, E, E)
+    del X, Y, Z
+    beta = beta.reshape(-1)
+    blocks = cfd.cfd_blocks_bind(scheme, mesh.n, mesh.dx, mesh.neighbors, g, cfd.CFD_F64)
+    nf, n_iter = spec["nf"], spec["n_iter"]
+    nint = int(sum(int(n) ** 3 for n in mesh.n))
+    units = nint * nf
+    out = torch.empty(units, dtype=torch.float64, device=dev)
+    ws = cfd.cfd_biased_workspace(blocks, nf, n_iter)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        cfd.cfd_exchange_ghosts(blocks, fields, nf, stream)
+        cfd.cfd_advect(blocks, fields, nf, beta, cfd.CFD_FP64_BANDED, n_iter, out, work, stream)
+
+    for _ in range(args.warmup):
+        step()
+    cfd.cfd_sync_status(blocks, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    launches0 = cfd.cfd_kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ms_step = timed(step, args.steps, stream, torch)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    cfd.cfd_sync_status(blocks, stream)
+    launches = cfd.cfd_kernel_launches() - launches0
+    prof_steps = max(3, min(args.steps, 50))
+    cfd.cfd_profile_enable(True)
+    torch.cuda.synchronize()
+    ms_prof = timed(step, prof_steps, stream, torch)
+    prof = {name: cfd.cfd_profile_read(fid) for name, fid in cfd.KERNEL_FAMILIES.items()}
+    cfd.cfd_profile_enable(False)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = units * world / (ms_step * 1e-3) / 1e9
+
+    nl, tl = prof["biased"]
+    fl = advect_flops_per_point_axis() * 3 * (n_iter + 1) * units * prof_steps
+    achieved = fl / (tl * 1e-3) / 1e9
+    byts = (16 + 24 / nf) * units * prof_steps                  # f and out once, beta once for all fields
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roof = {"kernel": "k_biased (FP64 upwind bidiagonal pencil solves)", "bound": "alu",
+            "achieved": round(achieved, 2), "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+            "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
+            "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table)",
+            "flops_per_point_field": advect_flops_per_point_axis() * 3 * (n_iter + 1),
+            "hbm_achieved_gbs": round(byts / (tl * 1e-3) / 1e9, 1), "hbm_peak_gbs": hbm,
+            "algorithmic_bytes_per_point_field": round(16 + 24 / nf, 2),
+            "traffic": None, "launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
+            "share_of_step": round(tl / (ms_prof * prof_steps), 4),
+            "events_region": {"steps": prof_steps, "ms_per_step": round(ms_prof, 5)}}
+
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty(fields.numel(), dtype=fields.dtype, pin_memory=True)
+        host_in.copy_(fields)
+        host_out = torch.empty(out.numel(), dtype=out.dtype, pin_memory=True)
+
+        def step_e2e():
+            fields.copy_(host_in, non_blocking=True)
+            step()
+            host_out.copy_(out, non_blocking=True)
+
+        step_e2e()
+        torch.cuda.synchronize()
+        ms_e2e = timed(step_e2e, max(3, min(20, args.steps // 10)), stream, torch)
+        e2e = {"value": round(units * world / (ms_e2e * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s",
+               "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+               "d2h_bytes_per_step": host_out.numel() * host_out.element_size(), "ms_per_step": round(ms_e2e, 4)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec)
+    if rank == 0:
+        in_bytes = fields.numel() * fields.element_size()
+        line = {
+            "metric": ADVECT_METRIC, "value": round(value, 4),
+            "unit": "Gpoint-ops/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded analytic fields and shift)",
+            "config": {"workload": args.workload, "path": "fp64_banded", "n_iter": n_iter, "fields": nf,
+                       "blocks": mesh.nblocks, "points_per_field": nint,
+                       "l2": "inputs larger than L2" if in_bytes > L2_BYTES else "inputs fit L2",
+                       "input_bytes": in_bytes, "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_wave(args, spec):
     """The RK4 wave driver: Gpoint-ops/s (3 second-derivative ops x points x 4 stages per step),
     steps/s, and the phase and amplitude errors of every plane-wave mode against the exact
@@ -722,7 +913,8 @@ def run_reference(args, spec, rank):
         vals.append(cpu_baseline(spec, seconds=2.0))
     el = time.perf_counter() - t0
     v = statistics.median(r["value"] for r in vals)
-    line = {"metric": METRIC, "value": round(v, 6), "unit": "Gpoint-ops/s", "n_gpus": args.gpus,
+    line = {"metric": ADVECT_METRIC if spec["kind"] == "advect" else METRIC, "value": round(v, 6),
+            "unit": "Gpoint-ops/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded analytic fields)", "impl": "reference",
