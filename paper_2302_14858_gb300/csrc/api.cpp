@@ -545,7 +545,7 @@ cfd_status cfd_blocks_bind(cfd_scheme_t scheme, int nblocks, const int *block_n,
     B->ops.push_back(os);
     if (B->biased.present) {
       BiasedTables bt;
-      build_biased_tables(B->biased, kv.first, bt);
+      build_biased_tables(B->biased, kv.first, ng, bt);
       B->btab.push_back(bt);
     }
   }

@@ -14,12 +14,59 @@
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "cfd_internal.h"
 
 namespace cfd {
 
-void build_biased_tables(const BiasedCoef &c, int N, BiasedTables &T) {
+namespace {
+
+// One row of a biased block operator in dense form: the block system (closed: N rows,
+// Eq. closure_left_X or its mirror; iterated: N + kc rows with the value at k^c fixed,
+// Eq. iter_left_X) solved for every right-hand-side column (f at ghost-extended index j,
+// and the fixed value as column E) in long double; returns the row of local index k.
+void biased_row(const BiasedCoef &c, int N, int g, int side, bool iter, int k_out, long double *row,
+                long double *coup) {
+  const int E = N + 2 * g, kc = c.kc, n = iter ? N + kc : N;
+  const int k0 = (iter && side > 0) ? -kc : 0;   // local index of unknown 0
+  std::vector<long double> A((size_t)n * n, 0), X((size_t)n * (E + 1), 0);
+  for (int u = 0; u < n; ++u) {
+    const int k = k0 + u;
+    A[(size_t)u * n + u] = 1;
+    if (iter && ((side > 0 && u == 0) || (side < 0 && u == n - 1))) {
+      X[(size_t)u * (E + 1) + E] = 1;               // fixed node
+      continue;
+    }
+    const bool clo = !iter && ((side > 0 && k == 0) || (side < 0 && k == N - 1));
+    if (side > 0) A[(size_t)u * n + (clo ? u + 1 : u - 1)] = clo ? c.csup : c.a;
+    else A[(size_t)u * n + (clo ? u - 1 : u + 1)] = clo ? c.csup : c.a;
+    const double *co = clo ? c.cl : c.rhs;
+    for (int m = -kBOff; m <= kBOff; ++m) {
+      const double v = co[m + kBOff];
+      if (v == 0) continue;
+      const int j = side > 0 ? k + m + g : k - m + g;   // mirror: -alpha_m at offset -m
+      X[(size_t)u * (E + 1) + j] += side > 0 ? v : -v;
+    }
+  }
+  // Gaussian elimination without pivoting (unit diagonal, |a|, |a csup| < 1)
+  for (int col = 0; col < n; ++col)
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const long double f = A[(size_t)r * n + col] / A[(size_t)col * n + col];
+      if (f == 0) continue;
+      for (int q = 0; q < n; ++q) A[(size_t)r * n + q] -= f * A[(size_t)col * n + q];
+      for (int q = 0; q <= E; ++q) X[(size_t)r * (E + 1) + q] -= f * X[(size_t)col * (E + 1) + q];
+    }
+  const int u = k_out - k0;
+  const long double d = A[(size_t)u * n + u];
+  for (int j = 0; j < E; ++j) row[j] = X[(size_t)u * (E + 1) + j] / d;
+  *coup = X[(size_t)u * (E + 1) + E] / d;
+}
+
+}  // namespace
+
+void build_biased_tables(const BiasedCoef &c, int N, int g, BiasedTables &T) {
   memset(&T, 0, sizeof(T));
   T.N = N;
   T.kc = c.kc;
@@ -36,6 +83,17 @@ void build_biased_tables(const BiasedCoef &c, int N, BiasedTables &T) {
     T.rhs[i] = c.rhs[i];
     T.clo[i] = c.cl[i];
   }
+  const int E = N + 2 * g;
+  if (E > kMaxN + 16 || c.kc > N) return;   // refused later by the request checks
+  std::vector<long double> row(E);
+  long double coup;
+  for (int side = 0; side < 2; ++side)
+    for (int it = 0; it < 2; ++it) {
+      const int sg = side == 0 ? 1 : -1;
+      biased_row(c, N, g, sg, it == 1, sg > 0 ? N - c.kc : c.kc - 1, row.data(), &coup);
+      for (int j = 0; j < E; ++j) T.hrow[side][it][j] = (double)row[j];
+      if (it == 1) T.hc[side] = (double)coup;
+    }
 }
 
 namespace {
@@ -43,6 +101,16 @@ namespace {
 __device__ __forceinline__ int dir_index(int dz, int dy, int dx) {
   int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
   return r > 13 ? r - 1 : r;
+}
+
+// 1 if v > 0, 2 if v < 0, 0 if v is a zero (integer tests on the bits)
+__device__ __forceinline__ int sign_bits(double v) {
+  const long long u = __double_as_longlong(v);
+  return (u << 1) == 0 ? 0 : (u < 0 ? 2 : 1);
+}
+__device__ __forceinline__ int sign_bits(float v) {
+  const int u = __float_as_int(v);
+  return (u << 1) == 0 ? 0 : (u < 0 ? 2 : 1);
 }
 
 // Stencil windows compiled in: interior offsets ILO..IHI and closure offsets
@@ -123,9 +191,46 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
   const bool do_p = P.mode != 1, do_m = P.mode != 0;
   const long long hp = (long long)np * 2;
 
+  if (!last) {
+    // halo-only pass: the two values the neighbours read next pass (d+ at N-kc, d- at kc-1),
+    // each one row of the dense block operator (closed for pass 0, iterated after that)
+    const int it = P.pass > 0 ? 1 : 0;
+    double *h = P.halo_out + ((long long)b * P.nf + q) * hp + 2 * p;
+    if (do_p) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc = fma(Tb.hrow[0][it][j], fv[j], acc);
+      double v = acc * scale;
+      if (it) v = fma(Tb.hc[0], P.halo_in[((long long)nlo * P.nf + q) * hp + 2 * p + 0], v);
+      h[0] = v;
+    }
+    if (do_m) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc = fma(Tb.hrow[1][it][j], fv[j], acc);
+      double v = acc * scale;
+      if (it) v = fma(Tb.hc[1], P.halo_in[((long long)nhi * P.nf + q) * hp + 2 * p + 1], v);
+      h[1] = v;
+    }
+    return;
+  }
+
+  // advect: a side whose shift sign does not occur on this pencil is not needed
+  const T *bet = P.mode == 2 ? static_cast<const T *>(P.beta) + 3ll * P.extpre[b] + (long long)(2 - ax) * box + tr +
+                                   (long long)G * sa
+                             : nullptr;
+  bool need_p = do_p, need_m = do_m;
+  if (P.mode == 2) {
+    int any = 0;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) any |= sign_bits(__ldg(bet + k * sa));
+    need_p = (any & 1) != 0;
+    need_m = (any & 2) != 0;
+  }
+
   // ---- right-biased derivative (S-), rows k = N-1 .. 0, kept in registers
   double dm[NT];
-  if (do_m) {
+  if (need_m) {
     const double ms = -scale;
     if (cyclic) {
       // y_{N-1} = r_{N-1}, y_k = r_k - a y_{k+1};  d_k = y_k + (-a)^{N-k} d_0, d_0 = y_0 / (1 - (-a)^N)
@@ -165,10 +270,6 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
   const long long oa = ostr(ax);
   T *o = static_cast<T *>(P.out) + (long long)P.nf * P.nops * P.intpre[b] + ((long long)q * P.nops + P.opidx) * n3 +
          (long long)t1 * ostr(P.t1) + (long long)t2 * ostr(P.t2);
-  // shift component of this axis (fields beta^x, beta^y, beta^z), interior rows
-  const T *bet = P.mode == 2 ? static_cast<const T *>(P.beta) + 3ll * P.extpre[b] + (long long)(2 - ax) * box + tr +
-                                   (long long)G * sa
-                             : nullptr;
   auto emit = [&](int k, double dp) {
     double v;
     if (P.mode == 0) {
@@ -176,17 +277,18 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
     } else if (P.mode == 1) {
       v = dm[k];
     } else {
-      const double bb = static_cast<double>(__ldg(bet + k * sa));
-      const double ab = fabs(bb);
-      v = 0.5 * (bb + ab) * dp + 0.5 * (bb - ab) * dm[k];
+      // beta_+ dp + beta_- dm: beta dp where beta > 0, beta dm where beta < 0, 0 where beta = 0
+      const T braw = __ldg(bet + k * sa);
+      const int sg = sign_bits(braw);
+      const double bb = static_cast<double>(braw);
+      v = sg == 1 ? bb * dp : (sg == 2 ? bb * dm[k] : 0.0);
     }
     if (P.accum) v = static_cast<double>(o[k * oa]) + v;
     o[k * oa] = static_cast<T>(v);
   };
 
   // ---- left-biased derivative (S+), rows k = 0 .. N-1, emitted as produced
-  double hpv = 0.0;  // d+ at N-kc for the right neighbour's next iterate
-  if (do_p) {
+  if (need_p) {
     if (cyclic) {
       // y_0 = r_0, y_k = r_k - a y_{k-1};  d_k = y_k + (-a)^{k+1} d_{N-1}, d_{N-1} = y_{N-1} / (1 - (-a)^N)
       double y = 0.0;
@@ -210,11 +312,9 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
         const double r0 = left_clo(0) * scale;
         const double r1 = left_int(1) * scale;
         d = fma(-Tb.csup, r1, r0) * Tb.inv01;
-        if (last) emit(0, d);
-        if (NT - Tb.kc == 0) hpv = d;
+        emit(0, d);
         d = fma(-a, d, r1);
-        if (last) emit(1, d);
-        if (NT - Tb.kc == 1) hpv = d;
+        emit(1, d);
         k0 = 2;
       } else {
         // iterated: d at k^c_- = -kc is the left neighbour's previous iterate
@@ -227,19 +327,12 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
       for (int k = 0; k < NT; ++k) {
         if (k < k0) continue;
         d = fma(-a, d, left_int(k) * scale);
-        if (last) emit(k, d);
-        if (k == NT - Tb.kc) hpv = d;
+        emit(k, d);
       }
     }
-  } else if (last) {
+  } else {
 #pragma unroll
     for (int k = 0; k < NT; ++k) emit(k, 0.0);
-  }
-
-  if (!last) {
-    double *h = P.halo_out + ((long long)b * P.nf + q) * hp + 2 * p;
-    if (do_p) h[0] = hpv;
-    if (do_m) h[1] = Tb.kc == 1 ? dm[0] : (Tb.kc == 2 ? dm[1] : dm[2]);
   }
 }
 

@@ -44,6 +44,11 @@ struct BiasedTables {
   double cyc_inv;          // 1 / (1 - (-a)^N): cyclic (single-block periodic) axis
   double rhs[kBTaps], clo[kBTaps];
   double pw[kMaxN + 1];    // (-a)^j
+  // Halo-only passes: row N-kc of the left-biased and row kc-1 of the right-biased block
+  // operator ([side][0 closed, 1 iterated][ghost-extended index]) and, for the iterated
+  // operator, the coefficient of the fixed value at k^c.
+  double hrow[2][2][kMaxN + 16];
+  double hc[2];
 };
 
 // One biased axis pass over a group of same-size blocks.
@@ -64,7 +69,7 @@ struct BiasedParams {
   int pass, last;
 };
 
-void build_biased_tables(const BiasedCoef &c, int N, BiasedTables &T);
+void build_biased_tables(const BiasedCoef &c, int N, int g, BiasedTables &T);
 
 // Everything one pencil solve needs for one (block size N, degree d).
 // Passed to kernels by value.

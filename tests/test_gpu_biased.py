@@ -155,13 +155,18 @@ def shift_fields():
 
 
 @pytest.mark.parametrize("name,g", [("X2_d1", 4), ("Q1034_1_d1", 4)])
-@pytest.mark.parametrize("n_iter", [0, 1])
-def test_advect_parity(lib, torch, name, g, n_iter):
-    """out = sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f on 4^3 blocks of 16^3, 3 fields."""
+@pytest.mark.parametrize("n_iter", [0, 1, 2])
+@pytest.mark.parametrize("shift", ["mixed", "one_sign"])
+def test_advect_parity(lib, torch, name, g, n_iter, shift):
+    """out = sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f on 4^3 blocks of 16^3, 3 fields.
+    "one_sign": beta^x > 0, beta^y = 0, beta^z < 0 everywhere (pencils that need one side, or none)."""
     NM, N, nf = 64, 16, 3
     fields = case_fields(21, nf)
     mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
-    _, _, bexts, bbuf = uniform_case(NM, N, g, shift_fields())
+    sf = shift_fields() if shift == "mixed" else [lambda X, Y, Z: 0.3 + 0.1 * np.sin(Y),
+                                                  lambda X, Y, Z: 0.0 * X,
+                                                  lambda X, Y, Z: -0.7 + 0.2 * np.cos(X)]
+    _, _, bexts, bbuf = uniform_case(NM, N, g, sf)
     blocks = bind(lib, name, mesh, g, lib.CFD_F64)
     dev = torch.device("cuda", 0)
     f_t = torch.from_numpy(buf).to(dev)
