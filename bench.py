@@ -50,6 +50,11 @@ WORKLOADS = {
     "box448x16_64x32_f22_fp32": dict(kind="boxinbox", nf=22, fields=4, dtype="f32", n_iter=0),
     # linear wave u_tt = Laplacian u, 256^3 as 512 blocks of 32^3, plane waves |k| <= 20, RK4, dt = 0.25 dx
     "wave256_b32_rk4": dict(kind="wave", NM=256, N=32, nf=2, dtype="f64", n_iter=0, modes=8, kmax=20.0),
+    # shifted wave (Eq. toyShiftWaveEqnSys, flat background) with a constant shift, 2S RK + Kreiss-Oliger,
+    # upwinded CCU X_2 advective terms, 256^3 as 512 blocks of 32^3, same plane waves (exact solution
+    # known: each mode's frequency is |k| - beta.k)
+    "shiftwave256_b32_x2_lsrk": dict(kind="wave", NM=256, N=32, nf=2, dtype="f64", n_iter=1, modes=8, kmax=20.0,
+                                     shift=(0.3, -0.2, 0.1)),
     # upwinded shift advection sum_i beta^i d_i f (Eq. biasderapproxadv) with the CCU X_2^-
     # scheme and its mirror (Tab. ccux_deg_one_col), 256^3 as 512 blocks of 32^3, 4 FP64 fields,
     # one iteration of Eq. iter_left_X
@@ -98,11 +103,12 @@ def shift_torch(X, Y, Z):
     return (torch.cos(X + 2 * Z) + 0.1, torch.sin(Y - X), 0.5 * torch.cos(3 * Y) * torch.sin(Z))
 
 
-def advect_flops_per_point_axis(n_taps=9, sides=2):
-    """FP64 flops per point, field and axis of one biased pass: per side the FMA chain over the
-    interior taps (2 n_taps), the 1/dx scale and the recurrence FMA; then the upwind combine
-    (|beta|, two weights, two products, one sum) and the accumulation over axes."""
-    return sides * (2 * n_taps + 1 + 2) + 7
+def advect_flops_per_point_axis(n_taps=9, n_iter=1, N=32, g=4):
+    """Algorithmic FP64 flops per point, field and axis of the upwinded term: the upwind side's
+    FMA chain over the interior taps (2 n_taps), the 1/dx scale, the recurrence FMA and the
+    product with beta; plus, per non-final pass of the iteration, the two halo values of a pencil
+    (one dense operator row of N + 2g FMAs per side) shared by its N points."""
+    return 2 * n_taps + 1 + 2 + 1 + n_iter * 2 * 2 * (N + 2 * g) / N
 
 
 # ------------------------------------------------------------------ clocks
@@ -271,6 +277,31 @@ def cpu_baseline(spec, seconds=12.0):
     s1 = C.Sch(1, e1["a"], tuple(e1["rhs"]), tuple(e1["closure"]))
     s2 = C.Sch(2, e2["a"], tuple(e2["rhs"]), tuple(e2["closure"]))
     g = 4
+    if spec["kind"] == "wave" and spec.get("shift") is not None:
+        from oracle import biased as BO
+        from oracle import timestep as TS
+        d = biased_desc()
+        bs = BO.Biased(d["a"], d["lo"], tuple(d["rhs"]), d["c_sup"], d["c_lo"], tuple(d["closure"]), d["kc"])
+        NS, N = 64, spec["N"]
+        pw = W.plane_waves(2302 + 5, spec["modes"], spec["kmax"])
+        dx = 2 * np.pi / NS
+        x = (np.arange(NS) + 0.5) * dx
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        p, k = pw.phi_at(0.0, X, Y, Z), pw.K_at(0.0, X, Y, Z)
+        beta = [np.full_like(X, v) for v in spec["shift"]]
+        coef = TS.lsrk2s_rk4_float()
+        units, reps = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            p, k = TS.shifted_wave_lsrk_step(p, k, beta, 0.25 * dx, coef, s2, bs, (dx, dx, dx), N, g,
+                                             spec["n_iter"], 0.04, 4)
+            units += 5 * NS ** 3 * 4
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        el = time.perf_counter() - t0
+        return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle shifted_wave_lsrk_step, {NS}^3 as {(NS // N) ** 3} blocks of {N}^3, {reps} steps"}
     if spec["kind"] == "wave":
         # sample: one RK4 step of the oracle on 64^3 as 8 blocks of 32^3 (units: 3 ops x points x 4 stages)
         NS, N = 64, spec["N"]
@@ -710,7 +741,14 @@ def run_advect(args, spec):
     value = units * world / (ms_step * 1e-3) / 1e9
 
     nl, tl = prof["biased"]
-    fl = advect_flops_per_point_axis() * 3 * (n_iter + 1) * units * prof_steps
+    fpp = advect_flops_per_point_axis(9, n_iter, N, g) * 3
+    fl = fpp * units * prof_steps
+    # pencils along each axis on which the shift changes sign need both biased solves
+    bi = beta.view(mesh.nblocks, 3, E, E, E)[:, :, g:g + N, g:g + N, g:g + N]
+    mixed = []
+    for i, dim in ((0, 4), (1, 3), (2, 2)):      # beta^x along x (dim 4), beta^y along y, beta^z along z
+        comp = bi[:, i]
+        mixed.append(float(((comp > 0).any(dim=dim - 1) & (comp < 0).any(dim=dim - 1)).double().mean()))
     achieved = fl / (tl * 1e-3) / 1e9
     byts = (16 + 24 / nf) * units * prof_steps                  # f and out once, beta once for all fields
     peaks = {}
@@ -724,7 +762,10 @@ def run_advect(args, spec):
             "achieved": round(achieved, 2), "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
             "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
             "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table)",
-            "flops_per_point_field": advect_flops_per_point_axis() * 3 * (n_iter + 1),
+            "flops_per_point_field": round(fpp, 2),
+            "flops_definition": "upwind side only: 2 taps + scale + recurrence + beta product per axis, "
+                                "plus the halo rows of the non-final passes",
+            "mixed_sign_pencils_xyz": [round(v, 4) for v in mixed],
             "hbm_achieved_gbs": round(byts / (tl * 1e-3) / 1e9, 1), "hbm_peak_gbs": hbm,
             "algorithmic_bytes_per_point_field": round(16 + 24 / nf, 2),
             "traffic": None, "launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
@@ -808,11 +849,19 @@ def run_wave(args, spec):
 
     phi0, K0 = layout(plane(0.0, False)), layout(plane(0.0, True))
     d1, d2 = scheme_descs()
-    blocks = cfd.cfd_blocks_bind(cfd.cfd_scheme_create(d1, d2), mesh.n, mesh.dx, mesh.neighbors, g, cfd.CFD_F64)
+    scheme = cfd.cfd_scheme_create(d1, d2)
+    shift = spec.get("shift")
+    if shift is not None:
+        cfd.cfd_scheme_set_biased(scheme, biased_desc())
+        beta = torch.empty((mesh.nblocks, 3, E, E, E), dtype=torch.float64, device=dev)
+        for i, v in enumerate(shift):
+            beta[:, i] = float(v)
+        beta = beta.reshape(-1)
+    blocks = cfd.cfd_blocks_bind(scheme, mesh.n, mesh.dx, mesh.neighbors, g, cfd.CFD_F64)
     stream = torch.cuda.current_stream(dev)
     phi, K = phi0.clone(), K0.clone()
 
-    lsrk = args.integrator == "lsrk2s"
+    lsrk = args.integrator == "lsrk2s" or shift is not None
     if lsrk:
         # a 4-stage 4th-order member of the 2S family (coefficients solved from the order conditions)
         coef = ([0.0, 0.068841064670197562, 0.62754761399692844, -0.59911219706265022],
@@ -821,13 +870,17 @@ def run_wave(args, spec):
                 [1.0, 0.14874467817694941, -0.88063710498437737, 1.0])
 
     def one_step(prec, work):
-        if lsrk:
+        if shift is not None:
+            cfd.cfd_shifted_wave_lsrk_step(blocks, phi, K, beta, dt, coef, args.sigma, args.ko_r, prec, spec["n_iter"],
+                                           work, stream)
+        elif lsrk:
             cfd.cfd_wave_lsrk_step(blocks, phi, K, dt, coef, args.sigma, args.ko_r, prec, spec["n_iter"], work, stream)
         else:
             cfd.cfd_wave_rk_step(blocks, phi, K, dt, prec, spec["n_iter"], work, stream)
 
     def run(prec, steps, timed_region):
-        ws = (cfd.cfd_wave_lsrk_workspace if lsrk else cfd.cfd_wave_workspace)(blocks, prec, spec["n_iter"])
+        ws = (cfd.cfd_shifted_wave_workspace if shift is not None else
+              cfd.cfd_wave_lsrk_workspace if lsrk else cfd.cfd_wave_workspace)(blocks, prec, spec["n_iter"])
         work = torch.empty(ws, dtype=torch.uint8, device=dev)
         phi.copy_(phi0)
         K.copy_(K0)
@@ -852,6 +905,8 @@ def run_wave(args, spec):
         amp, ph = 0.0, 0.0
         for kv, A, p in zip(pw.k, pw.A, pw.phi):
             w = float(np.sqrt((kv ** 2).sum()))
+            if shift is not None:                    # shifted system: frequency |k| - beta.k
+                w -= float(sum(float(b) * float(kk) for b, kk in zip(shift, kv)))
             arg = float(kv[0]) * X + float(kv[1]) * Y + float(kv[2]) * Z
             c = complex((fg * torch.cos(arg)).mean().item() * 2.0, -(fg * torch.sin(arg)).mean().item() * 2.0)
             want = float(A) * complex(math.cos(float(p) - w * t), math.sin(float(p) - w * t))
@@ -873,7 +928,8 @@ def run_wave(args, spec):
         tt = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    units = 3 * NM ** 3 * 4
+    # 3 second-derivative ops per point and stage (+ the two upwinded advective terms when shifted)
+    units = (3 + (2 if shift is not None else 0)) * NM ** 3 * 4
     cpu = cpu_baseline(spec) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     compare = None
     if not args.no_compare and prec != PREC["fp64_banded"]:
@@ -889,8 +945,9 @@ def run_wave(args, spec):
             "data": "synthetic (seeded plane waves)",
             "config": {"workload": args.workload, "path": args.prec, "n_iter": spec["n_iter"], "blocks": mesh.nblocks,
                        "dt_over_dx": 0.25, "modes": spec["modes"], "kmax": spec["kmax"],
-                       "integrator": args.integrator,
+                       "integrator": "lsrk2s" if lsrk else args.integrator,
                        "ko": {"sigma": args.sigma, "r": args.ko_r} if lsrk else None,
+                       "shift": list(shift) if shift is not None else None,
                        "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
             "steps_per_s": round(1e3 / ms * world, 3), "t_final": args.steps * dt, **err,
             "compare": compare, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,

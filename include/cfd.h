@@ -332,6 +332,28 @@ cfd_status cfd_apply_biased(cfd_blocks_t blocks, const void *fields, int nfields
 cfd_status cfd_advect(cfd_blocks_t blocks, const void *fields, int nfields, const void *beta, cfd_precision prec,
                       int n_iter, void *out, void *work, size_t work_bytes, void *stream);
 
+/* Device workspace of cfd_shifted_wave_lsrk_step (bytes). */
+cfd_status cfd_shifted_wave_workspace(cfd_blocks_t blocks, cfd_precision prec, int n_iter, size_t *bytes);
+
+/*
+ * One step of the 2S method (cfd_lsrk_desc) for the shifted wave system of
+ * Eq. toyShiftWaveEqnSys with a flat background (gamma^{ij} = delta^{ij}):
+ *     F_Phi = beta^j d_j Phi + K + sum_i Q_i[Phi],
+ *     F_K   = beta^j d_j K + sum_i D2_i Phi + sum_i Q_i[K],
+ * where the advective terms beta^j d_j are the upwinded biased operators of
+ * cfd_advect (Eq. biasderapproxadv with c -> beta^j, as Sec. "Shifted wave
+ * equation" prescribes for biased schemes; FP64 banded whatever `prec`), the
+ * Laplacian uses the second-degree scheme with arithmetic `prec`, and Q_i
+ * is the Kreiss-Oliger term of cfd_wave_lsrk_step.  `beta`: three fields
+ * (beta^x, beta^y, beta^z) in the field layout, constant during the step
+ * (ghosts unused).  Needs a biased scheme (cfd_scheme_set_biased) and the
+ * second-degree scheme; n_iter applies to both.  Errors as
+ * cfd_wave_lsrk_step, plus the checks of cfd_advect.
+ */
+cfd_status cfd_shifted_wave_lsrk_step(cfd_blocks_t blocks, void *phi, void *K, const void *beta, double dt,
+                                      const cfd_lsrk_desc *rk, double sigma, int ko_r, cfd_precision prec,
+                                      int n_iter, void *work, size_t work_bytes, void *stream);
+
 /* Wait for `stream`, then read and clear the device status word of the
  * handle: CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_DEVICE_ASSERT. */
 cfd_status cfd_sync_status(cfd_blocks_t blocks, void *stream);

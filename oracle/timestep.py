@@ -22,6 +22,14 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   autonomous system every 4-stage 4th-order method advances a mode by the same
   polynomial 1 + z + z^2/2 + z^3/6 + z^4/24, so this member and classical ERK4
   agree there up to rounding.
+* The shifted wave system (Eq. toyShiftWaveEqnSys, flat background gamma^{ij} =
+  delta^{ij}): F_Phi = beta^j d_j Phi + K, F_K = beta^j d_j K + gamma^{ij} d_i d_j Phi, with
+  the advective terms upwinded by the biased schemes (Eq. biasderapproxadv with c -> beta,
+  Sec. "Shifted wave equation"), plus the Kreiss-Oliger terms.
+* ``shifted_wave_1d_operator``: the single-domain semi-discrete operator L of Eq.
+  sd_wave_ops in 1+1 dimensions (constant beta, centred circulant D^{(1)}, D^{(2)}), and
+  ``exp_integrate`` its exponential integration (the paper evaluates matrix exponentials
+  by the scaling-and-squaring method of its citation; scipy's expm implements that method).
 """
 from __future__ import annotations
 
@@ -211,3 +219,40 @@ def wave_rhs_ko(phi: np.ndarray, K: np.ndarray, s2, dx3, N: int, g: int, n_iter:
 def wave_lsrk_step(phi, K, dt, coef, s2, dx3, N, g, n_iter=0, sigma=0.0, r=4):
     """One 2S step of the wave system with Kreiss-Oliger dissipation."""
     return lsrk2s_step((phi, K), dt, coef, lambda st: wave_rhs_ko(st[0], st[1], s2, dx3, N, g, n_iter, sigma, r))
+
+
+# ---------------------------------------------------------------------------
+# Shifted wave system (Eq. toyShiftWaveEqnSys, flat background)
+# ---------------------------------------------------------------------------
+
+
+def shifted_wave_rhs(phi, K, beta, s2, b, dx3, N, g, n_iter, sigma, r):
+    """F_Phi = beta . grad Phi + K + sum_i Q_i[Phi], F_K = beta . grad K + Laplacian Phi +
+    sum_i Q_i[K] on global periodic (z, y, x) arrays; ``beta`` = (beta^x, beta^y, beta^z) global
+    arrays; the advective terms are ``oracle.biased.advect_uniform`` with the biased scheme ``b``."""
+    from oracle import biased as B
+    from oracle import cfd as C
+    fp, fk = wave_rhs_ko(phi, K, s2, dx3, N, g, n_iter, sigma, r)
+    bb = [C.global_to_blocks(v, N) for v in beta]
+    ap = C.blocks_to_global(B.advect_uniform(C.ghost_fill_3d(phi, N, g), bb, b, dx3, N, g, n_iter))
+    ak = C.blocks_to_global(B.advect_uniform(C.ghost_fill_3d(K, N, g), bb, b, dx3, N, g, n_iter))
+    return fp + ap, fk + ak
+
+
+def shifted_wave_lsrk_step(phi, K, beta, dt, coef, s2, b, dx3, N, g, n_iter=0, sigma=0.0, r=4):
+    """One 2S step of the shifted wave system with dissipation."""
+    return lsrk2s_step((phi, K), dt, coef,
+                       lambda st: shifted_wave_rhs(st[0], st[1], beta, s2, b, dx3, N, g, n_iter, sigma, r))
+
+
+def shifted_wave_1d_operator(D1: np.ndarray, D2: np.ndarray, beta: float) -> np.ndarray:
+    """L = [[beta D1, I], [D2, beta D1]] of Eq. sd_wave_ops acting on (Phi, K)."""
+    n = D1.shape[0]
+    return np.block([[beta * D1, np.eye(n)], [D2, beta * D1]])
+
+
+def exp_integrate(L: np.ndarray, U0: np.ndarray, t: float) -> np.ndarray:
+    """U(t) = exp(t L) U(0): formal solution of the semi-discrete linear system."""
+    import scipy.linalg as sl
+    return sl.expm(t * L) @ U0
+

@@ -433,7 +433,8 @@ cfd_status check_request(cfd_blocks_s *B, int nf, cfd_precision prec, int n_iter
 
 // axes: box axes in output order; mode 0/1 derivative (one op per axis), 2 advect (one op, summed)
 cfd_status run_biased(cfd_blocks_s *B, const void *fields, int nf, const void *beta, const int *axes, int naxes,
-                      int mode, int n_iter, int win, void *out, void *work, cudaStream_t st) {
+                      int mode, int n_iter, int win, void *out, void *work, cudaStream_t st, int out_nops = 0,
+                      int out_opidx = 0, bool accum_all = false) {
   double *halo[2] = {nullptr, nullptr};
   const size_t he = halo_elems(B, nf, n_iter);
   if (he) {
@@ -455,15 +456,15 @@ cfd_status run_biased(cfd_blocks_s *B, const void *fields, int nf, const void *b
     P.scale = B->d_scale;
     P.nblk = (int)B->groups[gi].size();
     P.nf = nf;
-    P.nops = mode == 2 ? 1 : naxes;
+    P.nops = out_nops > 0 ? out_nops : (mode == 2 ? 1 : naxes);
     P.mode = mode;
     for (int i = 0; i < naxes; ++i) {
       const int a = axes[i];
       P.axis = a;
       P.t1 = a == 0 ? 1 : 0;
       P.t2 = a == 2 ? 1 : 2;
-      P.opidx = mode == 2 ? 0 : i;
-      P.accum = (mode == 2 && i > 0) ? 1 : 0;
+      P.opidx = mode == 2 ? out_opidx : i;
+      P.accum = (mode == 2 && (i > 0 || accum_all)) ? 1 : 0;
       for (int pass = 0; pass <= n_iter; ++pass) {
         P.pass = pass;
         P.last = pass == n_iter;
@@ -489,6 +490,17 @@ cfd_status check_work(cfd_blocks_s *B, int nf, int n_iter, void *work, size_t wo
 }
 
 }  // namespace
+
+cfd_status advect_accumulate(cfd_blocks_s *B, const void *field, const void *beta, void *out, int out_nops,
+                             int out_opidx, int n_iter, void *work, size_t work_bytes, cudaStream_t st) {
+  int win;
+  cfd_status s = check_request(B, 1, CFD_FP64_BANDED, n_iter, &win);
+  if (s != CFD_OK) return s;
+  if ((s = check_work(B, 1, n_iter, work, work_bytes)) != CFD_OK) return s;
+  const int axes[3] = {2, 1, 0};
+  return run_biased(B, field, 1, beta, axes, 3, 2, n_iter, win, out, work, st, out_nops, out_opidx, true);
+}
+
 }  // namespace cfd
 
 using namespace cfd;

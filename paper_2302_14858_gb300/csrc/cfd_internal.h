@@ -168,6 +168,11 @@ enum KernelFamily { KF_EXCHANGE = 0, KF_LINE = 1, KF_RK = 2, KF_DENSE = 3, KF_HA
 void launch_begin(int family, cudaStream_t st);
 void launch_end(int family, cudaStream_t st);
 
+// biased.cu: out[slot out_opidx of out_nops per block] += sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f
+// for one FP64 field (FP64 banded; `work` as cfd_biased_workspace(B, 1, n_iter))
+cfd_status advect_accumulate(cfd_blocks_s *B, const void *field, const void *beta, void *out, int out_nops,
+                             int out_opidx, int n_iter, void *work, size_t work_bytes, cudaStream_t st);
+
 // kernels (banded.cu)
 cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nfields, cudaStream_t st);
 cfd_status launch_line(const LineParams &P, const LineTables &T, cudaStream_t st, cfd_dtype dt);

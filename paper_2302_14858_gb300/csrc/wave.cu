@@ -312,37 +312,46 @@ extern "C" cfd_status cfd_wave_lsrk_workspace(cfd_blocks_t B, cfd_precision prec
   WaveLayout L;
   cfd_status s = wave_layout(B, prec, n_iter, L);
   if (s != CFD_OK) return s;
-  *bytes = al(L.in * 8) * 2 + al(3 * L.in * 8) + L.apply + 256;
+  *bytes = al(L.in * 8) * 2 + al(3 * L.in * 8) + al(L.apply) + 256;
   return CFD_OK;
 }
 
-extern "C" cfd_status cfd_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, double dt, const cfd_lsrk_desc *rk,
-                                         double sigma, int ko_r, cfd_precision prec, int n_iter, void *work,
-                                         size_t work_bytes, void *stream) {
-  if (!B || !phi || !K || !work || !rk) { set_error("cfd_wave_lsrk_step: bad argument"); return CFD_ERR_ARG; }
-  if (rk->stages < 1 || rk->stages > 8 || !rk->gamma1 || !rk->gamma2 || !rk->beta || !rk->delta) {
-    set_error("cfd_wave_lsrk_step: 1..8 stages with all four coefficient arrays");
-    return CFD_ERR_ARG;
-  }
-  if (!(sigma >= 0) || (sigma > 0 && (ko_r < 1 || ko_r > B->ng || ko_r > 6))) {
-    set_error("cfd_wave_lsrk_step: sigma >= 0 and 1 <= ko_r <= min(ng, 6)");
-    return CFD_ERR_ARG;
-  }
-  if (B->dtype != CFD_F64) { set_error("cfd_wave_lsrk_step: FP64 fields only"); return CFD_ERR_UNSUPPORTED; }
-  if (!B->s[1].present) { set_error("cfd_wave_lsrk_step: needs the second-degree scheme"); return CFD_ERR_ARG; }
+namespace cfd {
+namespace {
+
+// One 2S step of the wave system with Kreiss-Oliger terms; with `beta` the shifted system of
+// Eq. toyShiftWaveEqnSys (flat gamma): the upwinded advective terms beta^i d_i Phi and
+// beta^i d_i K are added to F_Phi and F_K.
+cfd_status lsrk_impl(const char *who, cfd_blocks_s *B, void *phi, void *K, const void *beta, double dt,
+                     const cfd_lsrk_desc *rk, double sigma, int ko_r, cfd_precision prec, int n_iter, void *work,
+                     size_t work_bytes, cudaStream_t st) {
+  auto fail = [&](cfd_status code, const char *msg) {
+    set_error(std::string(who) + ": " + msg);
+    return code;
+  };
+  if (!B || !phi || !K || !work || !rk) return fail(CFD_ERR_ARG, "bad argument");
+  if (rk->stages < 1 || rk->stages > 8 || !rk->gamma1 || !rk->gamma2 || !rk->beta || !rk->delta)
+    return fail(CFD_ERR_ARG, "1..8 stages with all four coefficient arrays");
+  if (!(sigma >= 0) || (sigma > 0 && (ko_r < 1 || ko_r > B->ng || ko_r > 6)))
+    return fail(CFD_ERR_ARG, "sigma >= 0 and 1 <= ko_r <= min(ng, 6)");
+  if (B->dtype != CFD_F64) return fail(CFD_ERR_UNSUPPORTED, "FP64 fields only");
+  if (!B->s[1].present) return fail(CFD_ERR_ARG, "needs the second-degree scheme");
+  if (beta && !B->biased.present) return fail(CFD_ERR_ARG, "the shift terms need a biased scheme (cfd_scheme_set_biased)");
   for (int v : B->nbr)
-    if (v < 0) { set_error("cfd_wave_lsrk_step: every ghost region needs a neighbour"); return CFD_ERR_UNSUPPORTED; }
+    if (v < 0) return fail(CFD_ERR_UNSUPPORTED, "every ghost region needs a neighbour");
   WaveLayout L;
   cfd_status s = wave_layout(B, prec, n_iter, L);
   if (s != CFD_OK) return s;
-  const size_t need = al(L.in * 8) * 2 + al(3 * L.in * 8) + L.apply + 256;
-  if (work_bytes < need) { set_error("cfd_wave_lsrk_step: workspace too small"); return CFD_ERR_ARG; }
-  cudaStream_t st = (cudaStream_t)stream;
+  size_t bws = 0;
+  if (beta && (s = cfd_biased_workspace(B, 1, n_iter, &bws)) != CFD_OK) return s;
+  const size_t need = al(L.in * 8) * 2 + al(3 * L.in * 8) + al(L.apply) + bws + 256;
+  if (work_bytes < need) return fail(CFD_ERR_ARG, "workspace too small");
   char *base = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
   double *s2p = (double *)base;  base += al(L.in * 8);
   double *s2k = (double *)base;  base += al(L.in * 8);
   double *lap = (double *)base;  base += al(3 * L.in * 8);
-  void *aw = base;
+  void *aw = base;               base += al(L.apply);
+  void *bw = bws ? (void *)base : nullptr;
   const unsigned ops = CFD_OP_DXX | CFD_OP_DYY | CFD_OP_DZZ;
   const bool ko_on = sigma > 0;
   RhsArgs R;
@@ -371,9 +380,9 @@ extern "C" cfd_status cfd_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, dou
     else k_wave_rhs<decltype(nc)::value, float><<<grid, 256, 0, st>>>(A);
   };
   for (int stage = 0; stage < rk->stages; ++stage) {
-    if ((s = cfd_exchange_ghosts(B, phi, 1, stream)) != CFD_OK) return s;
-    if (ko_on && (s = cfd_exchange_ghosts(B, K, 1, stream)) != CFD_OK) return s;
-    if ((s = cfd_apply(B, phi, 1, ops, prec, n_iter, lap, aw, L.apply, stream)) != CFD_OK) return s;
+    if ((s = cfd_exchange_ghosts(B, phi, 1, st)) != CFD_OK) return s;
+    if ((ko_on || beta) && (s = cfd_exchange_ghosts(B, K, 1, st)) != CFD_OK) return s;
+    if ((s = cfd_apply(B, phi, 1, ops, prec, n_iter, lap, aw, L.apply, st)) != CFD_OK) return s;
     for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
       const int N = B->sizes[gi];
       const long long n3 = (long long)N * N * N;
@@ -397,6 +406,16 @@ extern "C" cfd_status cfd_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, dou
       else launch1(std::integral_constant<int, 0>(), A, grid);
       launch_end(KF_RK, st);
       if ((s = cuda_fail(cudaGetLastError(), "k_wave_rhs launch")) != CFD_OK) return s;
+    }
+    if (beta) {
+      // F_Phi (slot 1) += beta . grad Phi, F_K (slot 0) += beta . grad K, upwinded
+      if ((s = advect_accumulate(B, phi, beta, lap, 3, 1, n_iter, bw, bws, st)) != CFD_OK) return s;
+      if ((s = advect_accumulate(B, K, beta, lap, 3, 0, n_iter, bw, bws, st)) != CFD_OK) return s;
+    }
+    for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
+      const int N = B->sizes[gi];
+      const long long n3 = (long long)N * N * N;
+      dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)B->groups[gi].size());
       UpdArgs U;
       U.phi = (double *)phi;
       U.K = (double *)K;
@@ -422,4 +441,33 @@ extern "C" cfd_status cfd_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, dou
     }
   }
   return CFD_OK;
+}
+
+}  // namespace
+}  // namespace cfd
+
+extern "C" cfd_status cfd_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, double dt, const cfd_lsrk_desc *rk,
+                                         double sigma, int ko_r, cfd_precision prec, int n_iter, void *work,
+                                         size_t work_bytes, void *stream) {
+  return lsrk_impl("cfd_wave_lsrk_step", B, phi, K, nullptr, dt, rk, sigma, ko_r, prec, n_iter, work, work_bytes,
+                   (cudaStream_t)stream);
+}
+
+extern "C" cfd_status cfd_shifted_wave_workspace(cfd_blocks_t B, cfd_precision prec, int n_iter, size_t *bytes) {
+  if (!B || !bytes) { set_error("cfd_shifted_wave_workspace: bad argument"); return CFD_ERR_ARG; }
+  WaveLayout L;
+  cfd_status s = wave_layout(B, prec, n_iter, L);
+  if (s != CFD_OK) return s;
+  size_t bws = 0;
+  if ((s = cfd_biased_workspace(B, 1, n_iter, &bws)) != CFD_OK) return s;
+  *bytes = al(L.in * 8) * 2 + al(3 * L.in * 8) + al(L.apply) + bws + 256;
+  return CFD_OK;
+}
+
+extern "C" cfd_status cfd_shifted_wave_lsrk_step(cfd_blocks_t B, void *phi, void *K, const void *beta, double dt,
+                                                 const cfd_lsrk_desc *rk, double sigma, int ko_r, cfd_precision prec,
+                                                 int n_iter, void *work, size_t work_bytes, void *stream) {
+  if (!beta) { set_error("cfd_shifted_wave_lsrk_step: beta is null (use cfd_wave_lsrk_step)"); return CFD_ERR_ARG; }
+  return lsrk_impl("cfd_shifted_wave_lsrk_step", B, phi, K, beta, dt, rk, sigma, ko_r, prec, n_iter, work,
+                   work_bytes, (cudaStream_t)stream);
 }

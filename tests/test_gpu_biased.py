@@ -227,3 +227,65 @@ def test_rejections(lib, torch):
     with pytest.raises(lib.CfdError):
         lib.cfd_scheme_set_biased(s5, bad)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec,n_iter", [(0, 0), (0, 1), (2, 1)])
+def test_shifted_wave_lsrk_parity(lib, torch, prec, n_iter):
+    """Two 2S steps of the shifted wave system (Eq. toyShiftWaveEqnSys, flat background) with a
+    mixed-sign shift field and Kreiss-Oliger dissipation vs the oracle."""
+    from oracle import timestep as T
+    from paper_2302_14858_gb300 import workloads as W
+    from tests.helpers import oracle_sch
+    NM, N, g, sigma, r = 64, 16, 4, 0.04, 4
+    pw = W.plane_waves(19, 4, 10.0)
+    dx = 2 * np.pi / NM
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi0 = pw.phi_at(0.0, X, Y, Z) + 0.05 * np.cos(11 * X - 9 * Y + 7 * Z)
+    K0 = pw.K_at(0.0, X, Y, Z)
+    beta_g = [f(X, Y, Z) for f in shift_fields()]
+    mesh, _, _, bbuf = uniform_case(NM, N, g, shift_fields())
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    lib.cfd_scheme_set_biased(s, SCHEMES["X2_d1"])
+    Bk = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    E = N + 2 * g
+    tp = torch.from_numpy(C.ghost_fill_3d(phi0, N, g).reshape(-1).copy()).cuda()
+    tk = torch.from_numpy(C.ghost_fill_3d(K0, N, g).reshape(-1).copy()).cuda()
+    tb = torch.from_numpy(bbuf).cuda()
+    work = torch.empty(lib.cfd_shifted_wave_workspace(Bk, prec, n_iter), dtype=torch.uint8, device="cuda")
+    coef = T.lsrk2s_rk4_float()
+    dt = 0.25 * dx
+    s2 = oracle_sch("Q13_1_d2")
+    b = biased_of("X2_d1")
+    p, k = phi0, K0
+    for _ in range(2):
+        lib.cfd_shifted_wave_lsrk_step(Bk, tp, tk, tb, dt, coef, sigma, r, prec, n_iter, work)
+        p, k = T.shifted_wave_lsrk_step(p, k, beta_g, dt, coef, s2, b, (dx, dx, dx), N, g, n_iter, sigma, r)
+    lib.cfd_sync_status(Bk)
+    nb = NM // N
+    I = slice(g, g + N)
+    gp = C.blocks_to_global(tp.cpu().numpy().reshape(mesh.nblocks, E, E, E)[:, I, I, I].reshape(nb, nb, nb, N, N, N))
+    gk = C.blocks_to_global(tk.cpu().numpy().reshape(mesh.nblocks, E, E, E)[:, I, I, I].reshape(nb, nb, nb, N, N, N))
+    tol = 1e-12 if prec == 0 else 1e-7
+    assert rel_max(gp, p) < tol, rel_max(gp, p)
+    assert rel_max(gk, k) < tol, rel_max(gk, k)
+    # the shift terms are visible: the unshifted step differs well beyond the tolerance
+    p0, _ = T.wave_lsrk_step(phi0, K0, dt, coef, s2, (dx, dx, dx), N, g, n_iter, sigma, r)
+    p1, _ = T.shifted_wave_lsrk_step(phi0, K0, beta_g, dt, coef, s2, b, (dx, dx, dx), N, g, n_iter, sigma, r)
+    assert rel_max(p0, p1) > 1e-3
+
+
+def test_shifted_wave_rejections(lib, torch):
+    from oracle import timestep as T
+    NM, N, g = 32, 16, 4
+    mesh, _, _, bbuf = uniform_case(NM, N, g, shift_fields())
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))        # no biased scheme
+    Bk = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    E = N + 2 * g
+    t = torch.zeros(mesh.nblocks * E ** 3, dtype=torch.float64, device="cuda")
+    tb = torch.from_numpy(bbuf).cuda()
+    work = torch.empty(lib.cfd_shifted_wave_workspace(Bk, 0, 0), dtype=torch.uint8, device="cuda")
+    with pytest.raises(lib.CfdError) as e:
+        lib.cfd_shifted_wave_lsrk_step(Bk, t, t.clone(), tb, 0.01, T.lsrk2s_rk4_float(), 0.0, 4, 0, 0, work)
+    assert e.value.status == lib.CFD_ERR_ARG
+    torch.cuda.synchronize()
