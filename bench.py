@@ -703,13 +703,15 @@ def run_advect(args, spec):
     nint = int(sum(int(n) ** 3 for n in mesh.n))
     units = nint * nf
     out = torch.empty(units, dtype=torch.float64, device=dev)
-    ws = cfd.cfd_biased_workspace(blocks, nf, n_iter)
+    prec = PREC[args.prec]
+    ws = max(cfd.cfd_biased_workspace(blocks, nf, prec, n_iter),
+             cfd.cfd_biased_workspace(blocks, nf, cfd.CFD_FP64_BANDED, n_iter))
     work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def step(p=prec, o=out):
         cfd.cfd_exchange_ghosts(blocks, fields, nf, stream)
-        cfd.cfd_advect(blocks, fields, nf, beta, cfd.CFD_FP64_BANDED, n_iter, out, work, stream)
+        cfd.cfd_advect(blocks, fields, nf, beta, p, n_iter, o, work, stream)
 
     for _ in range(args.warmup):
         step()
@@ -743,13 +745,13 @@ def run_advect(args, spec):
     nl, tl = prof["biased"]
     fpp = advect_flops_per_point_axis(9, n_iter, N, g) * 3
     fl = fpp * units * prof_steps
+    ndl, tdl = prof["dense"]
     # pencils along each axis on which the shift changes sign need both biased solves
     bi = beta.view(mesh.nblocks, 3, E, E, E)[:, :, g:g + N, g:g + N, g:g + N]
     mixed = []
     for i, dim in ((0, 4), (1, 3), (2, 2)):      # beta^x along x (dim 4), beta^y along y, beta^z along z
         comp = bi[:, i]
         mixed.append(float(((comp > 0).any(dim=dim - 1) & (comp < 0).any(dim=dim - 1)).double().mean()))
-    achieved = fl / (tl * 1e-3) / 1e9
     byts = (16 + 24 / nf) * units * prof_steps                  # f and out once, beta once for all fields
     peaks = {}
     try:
@@ -758,19 +760,53 @@ def run_advect(args, spec):
     except OSError:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    roof = {"kernel": "k_biased (FP64 upwind bidiagonal pencil solves)", "bound": "alu",
-            "achieved": round(achieved, 2), "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-            "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
-            "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table)",
-            "flops_per_point_field": round(fpp, 2),
-            "flops_definition": "upwind side only: 2 taps + scale + recurrence + beta product per axis, "
-                                "plus the halo rows of the non-final passes",
-            "mixed_sign_pencils_xyz": [round(v, 4) for v in mixed],
-            "hbm_achieved_gbs": round(byts / (tl * 1e-3) / 1e9, 1), "hbm_peak_gbs": hbm,
-            "algorithmic_bytes_per_point_field": round(16 + 24 / nf, 2),
-            "traffic": None, "launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
-            "share_of_step": round(tl / (ms_prof * prof_steps), 4),
-            "events_region": {"steps": prof_steps, "ms_per_step": round(ms_prof, 5)}}
+    if prec != cfd.CFD_FP64_BANDED:
+        # k_dense: per axis the field is read once and both biased derivatives written once; each
+        # halo-only pass of the iteration reads the field again.  The blend kernel reads the
+        # upwind derivative of each axis and the three shift components, and writes the term.
+        elem = fields.element_size()
+        per_pf = 3 * (3 + n_iter) * elem
+        ach = per_pf * units * prof_steps / (tdl * 1e-3) / 1e9
+        comb_b = (3 + 3 + 1) * elem * units * prof_steps
+        roof = {"kernel": "k_dense (tcgen05 BF16 digit-slice GEMM, biased operators D+ and D-)", "bound": "hbm",
+                "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_point_field": round(per_pf, 2), "traffic": None,
+                "launches_per_step": ndl / prof_steps, "avg_launch_ms": round(tdl / max(ndl, 1), 5),
+                "share_of_step": round(tdl / (ms_prof * prof_steps), 4),
+                "blend": {"kernel": "k_advect_combine", "launches_per_step": nl / prof_steps,
+                          "ms_per_step": round(tl / prof_steps, 4),
+                          "hbm_gbs": round(comb_b / (tl * 1e-3) / 1e9, 1) if tl > 0 else None},
+                "events_region": {"steps": prof_steps, "ms_per_step": round(ms_prof, 5)}}
+    else:
+        achieved = fl / (tl * 1e-3) / 1e9
+        roof = {"kernel": "k_biased (FP64 upwind bidiagonal pencil solves)", "bound": "alu",
+                "achieved": round(achieved, 2), "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                "frac": round(achieved / FP64_NOMINAL_GFLOPS, 4),
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (profiling recipe table)",
+                "flops_per_point_field": round(fpp, 2),
+                "flops_definition": "upwind side only: 2 taps + scale + recurrence + beta product per axis, "
+                                    "plus the halo rows of the non-final passes",
+                "mixed_sign_pencils_xyz": [round(v, 4) for v in mixed],
+                "hbm_achieved_gbs": round(byts / (tl * 1e-3) / 1e9, 1), "hbm_peak_gbs": hbm,
+                "algorithmic_bytes_per_point_field": round(16 + 24 / nf, 2),
+                "traffic": None, "launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
+                "share_of_step": round(tl / (ms_prof * prof_steps), 4),
+                "events_region": {"steps": prof_steps, "ms_per_step": round(ms_prof, 5)}}
+
+    compare = None
+    if not args.no_compare and prec != cfd.CFD_FP64_BANDED:
+        ref = torch.empty_like(out)
+        step(cfd.CFD_FP64_BANDED, ref)
+        torch.cuda.synchronize()
+        ms64 = timed(lambda: step(cfd.CFD_FP64_BANDED, ref), args.compare_steps, stream, torch)
+        step()
+        torch.cuda.synchronize()
+        o4, r4 = out.view(-1, nf, N ** 3), ref.view(-1, nf, N ** 3)
+        rel = [float((o4[:, q] - r4[:, q]).abs().max() / r4[:, q].abs().max()) for q in range(nf)]
+        compare = {"fp64_banded": {"value": round(units / (ms64 * 1e-3) / 1e9, 4), "ms_per_step": round(ms64, 4)},
+                   "speedup_vs_fp64_banded": round(ms64 / ms_step, 3), "max_rel_err_vs_fp64_banded": max(rel)}
+        del ref
 
     e2e = None
     if not args.no_e2e:
@@ -799,11 +835,12 @@ def run_advect(args, spec):
             "unit": "Gpoint-ops/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded analytic fields and shift)",
-            "config": {"workload": args.workload, "path": "fp64_banded", "n_iter": n_iter, "fields": nf,
+            "config": {"workload": args.workload, "path": args.prec, "n_iter": n_iter, "fields": nf,
                        "blocks": mesh.nblocks, "points_per_field": nint,
                        "l2": "inputs larger than L2" if in_bytes > L2_BYTES else "inputs fit L2",
                        "input_bytes": in_bytes, "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roof, "compare": compare, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk,
         }
         print(json.dumps(line))
     if world > 1:

@@ -297,8 +297,10 @@ typedef struct cfd_biased_desc {
  * builds its per-block-size tables).  Errors: CFD_ERR_ARG. */
 cfd_status cfd_scheme_set_biased(cfd_scheme_t scheme, const cfd_biased_desc *desc);
 
-/* Device workspace of cfd_apply_biased / cfd_advect (bytes; 0 without iteration). */
-cfd_status cfd_biased_workspace(cfd_blocks_t blocks, int nfields, int n_iter, size_t *bytes);
+/* Device workspace of cfd_apply_biased / cfd_advect for this arithmetic (bytes; 0 for
+ * CFD_FP64_BANDED without iteration; the tensor-core form keeps both biased derivatives of
+ * every axis, 6 N^3 values per block and field, for the upwind blend). */
+cfd_status cfd_biased_workspace(cfd_blocks_t blocks, int nfields, cfd_precision prec, int n_iter, size_t *bytes);
 
 /*
  * Biased first derivatives of ghost-filled fields: for every block, field
@@ -308,10 +310,14 @@ cfd_status cfd_biased_workspace(cfd_blocks_t blocks, int nfields, int n_iter, si
  * Jacobi: every block reads its neighbours' iterate i-1).  An axis along
  * which a block is its own neighbour on both faces uses the undecomposed
  * cyclic scheme.  Output layout as cfd_apply (axes in bit order).
- *   prec   CFD_FP64_BANDED (the only arithmetic of this path).
+ *   prec   CFD_FP64_BANDED: per-pencil FP64 bidiagonal solves;
+ *          CFD_TC_BF16_EXACT / CFD_TC_BF16X3: the dense operators
+ *          D = A^-1 B of the same block systems on the tensor cores (exact
+ *          integer digit slices, or BF16 hi/lo), with the iteration as
+ *          d = D_1 f + c d^c (blocks of 16^3 or 32^3, uniform spacing).
  * Errors: CFD_ERR_ARG (no biased scheme bound, bad mask/side, workspace),
  * CFD_ERR_UNSUPPORTED (stencil support, iteration without face neighbours,
- * other precisions), CFD_ERR_CUDA.
+ * TF32, block sizes the tensor-core form does not cover), CFD_ERR_CUDA.
  */
 cfd_status cfd_apply_biased(cfd_blocks_t blocks, const void *fields, int nfields, unsigned axis_mask, int side,
                             cfd_precision prec, int n_iter, void *out, void *work, size_t work_bytes,
@@ -327,7 +333,8 @@ cfd_status cfd_apply_biased(cfd_blocks_t blocks, const void *fields, int nfields
  * right-biased one where beta^i < 0.  `beta` holds three fields (beta^x,
  * beta^y, beta^z) in the field layout (ghosts unused); `out` one N^3 array
  * per block and field.  Arithmetic as cfd_apply_biased; the three axis terms
- * are added in the order x, y, z.
+ * are added in the order x, y, z (the tensor-core form writes both biased
+ * derivatives of every axis to the workspace and blends them in one pass).
  */
 cfd_status cfd_advect(cfd_blocks_t blocks, const void *fields, int nfields, const void *beta, cfd_precision prec,
                       int n_iter, void *out, void *work, size_t work_bytes, void *stream);
@@ -342,8 +349,8 @@ cfd_status cfd_shifted_wave_workspace(cfd_blocks_t blocks, cfd_precision prec, i
  *     F_K   = beta^j d_j K + sum_i D2_i Phi + sum_i Q_i[K],
  * where the advective terms beta^j d_j are the upwinded biased operators of
  * cfd_advect (Eq. biasderapproxadv with c -> beta^j, as Sec. "Shifted wave
- * equation" prescribes for biased schemes; FP64 banded whatever `prec`), the
- * Laplacian uses the second-degree scheme with arithmetic `prec`, and Q_i
+ * equation" prescribes for biased schemes), the Laplacian uses the
+ * second-degree scheme, both with arithmetic `prec`, and Q_i
  * is the Kreiss-Oliger term of cfd_wave_lsrk_step.  `beta`: three fields
  * (beta^x, beta^y, beta^z) in the field layout, constant during the step
  * (ghosts unused).  Needs a biased scheme (cfd_scheme_set_biased) and the

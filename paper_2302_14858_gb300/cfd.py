@@ -104,7 +104,7 @@ class BiasedDesc(ctypes.Structure):
 
 _lib.cfd_scheme_set_biased.argtypes = [c_void_p, POINTER(BiasedDesc)]
 _lib.cfd_scheme_set_biased.restype = c_int
-_lib.cfd_biased_workspace.argtypes = [c_void_p, c_int, c_int, POINTER(c_size_t)]
+_lib.cfd_biased_workspace.argtypes = [c_void_p, c_int, c_int, c_int, POINTER(c_size_t)]
 _lib.cfd_biased_workspace.restype = c_int
 _lib.cfd_apply_biased.argtypes = [c_void_p, c_void_p, c_int, c_uint, c_int, c_int, c_int, c_void_p, c_void_p,
                                   c_size_t, c_void_p]
@@ -297,9 +297,9 @@ def cfd_scheme_set_biased(scheme: Scheme, d: dict):
     _check(_lib.cfd_scheme_set_biased(scheme.handle, ctypes.byref(desc)))
 
 
-def cfd_biased_workspace(blocks: Blocks, nfields: int, n_iter: int) -> int:
+def cfd_biased_workspace(blocks: Blocks, nfields: int, prec: int, n_iter: int) -> int:
     n = c_size_t()
-    _check(_lib.cfd_biased_workspace(blocks.handle, nfields, n_iter, ctypes.byref(n)))
+    _check(_lib.cfd_biased_workspace(blocks.handle, nfields, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 

@@ -20,15 +20,16 @@
 
 namespace cfd {
 
-namespace {
-
-// One row of a biased block operator in dense form: the block system (closed: N rows,
+// Biased block operator in dense form: the block system (closed: N rows,
 // Eq. closure_left_X or its mirror; iterated: N + kc rows with the value at k^c fixed,
-// Eq. iter_left_X) solved for every right-hand-side column (f at ghost-extended index j,
-// and the fixed value as column E) in long double; returns the row of local index k.
-void biased_row(const BiasedCoef &c, int N, int g, int side, bool iter, int k_out, long double *row,
-                long double *coup) {
-  const int E = N + 2 * g, kc = c.kc, n = iter ? N + kc : N;
+// Eq. iter_left_X; cyclic: the undecomposed periodic system) solved for every right-hand-side
+// column (f at ghost-extended index j, and the fixed value) in long double, without dx scaling.
+// W: N x E row-major (the N interior rows), coup: the N coefficients of the fixed value.
+void biased_operator(const BiasedCoef &c, int N, int g, int side, int kind, std::vector<long double> &W,
+                     std::vector<long double> &coup) {
+  const int E = N + 2 * g, kc = c.kc;
+  const bool iter = kind == 1, cyc = kind == 2;
+  const int n = iter ? N + kc : N;
   const int k0 = (iter && side > 0) ? -kc : 0;   // local index of unknown 0
   std::vector<long double> A((size_t)n * n, 0), X((size_t)n * (E + 1), 0);
   for (int u = 0; u < n; ++u) {
@@ -38,33 +39,48 @@ void biased_row(const BiasedCoef &c, int N, int g, int side, bool iter, int k_ou
       X[(size_t)u * (E + 1) + E] = 1;               // fixed node
       continue;
     }
-    const bool clo = !iter && ((side > 0 && k == 0) || (side < 0 && k == N - 1));
-    if (side > 0) A[(size_t)u * n + (clo ? u + 1 : u - 1)] = clo ? c.csup : c.a;
-    else A[(size_t)u * n + (clo ? u - 1 : u + 1)] = clo ? c.csup : c.a;
+    const bool clo = !iter && !cyc && ((side > 0 && k == 0) || (side < 0 && k == N - 1));
+    int off = side > 0 ? (clo ? 1 : -1) : (clo ? -1 : 1);
+    int col = u + off;
+    if (cyc) col = (col + n) % n;
+    A[(size_t)u * n + col] += clo ? c.csup : c.a;
     const double *co = clo ? c.cl : c.rhs;
     for (int m = -kBOff; m <= kBOff; ++m) {
       const double v = co[m + kBOff];
       if (v == 0) continue;
-      const int j = side > 0 ? k + m + g : k - m + g;   // mirror: -alpha_m at offset -m
-      X[(size_t)u * (E + 1) + j] += side > 0 ? v : -v;
+      int j = side > 0 ? k + m : k - m;             // mirror: -alpha_m at offset -m
+      if (cyc) j = ((j % N) + N) % N;               // periodic line: the interior point itself
+      X[(size_t)u * (E + 1) + j + g] += side > 0 ? v : -v;
     }
   }
-  // Gaussian elimination without pivoting (unit diagonal, |a|, |a csup| < 1)
-  for (int col = 0; col < n; ++col)
+  // Gauss-Jordan elimination with partial pivoting
+  for (int col = 0; col < n; ++col) {
+    int pr = col;
+    for (int r = col + 1; r < n; ++r)
+      if (fabsl(A[(size_t)r * n + col]) > fabsl(A[(size_t)pr * n + col])) pr = r;
+    if (pr != col) {
+      for (int q = 0; q < n; ++q) std::swap(A[(size_t)pr * n + q], A[(size_t)col * n + q]);
+      for (int q = 0; q <= E; ++q) std::swap(X[(size_t)pr * (E + 1) + q], X[(size_t)col * (E + 1) + q]);
+    }
+    const long double d = A[(size_t)col * n + col];
+    for (int q = 0; q < n; ++q) A[(size_t)col * n + q] /= d;
+    for (int q = 0; q <= E; ++q) X[(size_t)col * (E + 1) + q] /= d;
     for (int r = 0; r < n; ++r) {
       if (r == col) continue;
-      const long double f = A[(size_t)r * n + col] / A[(size_t)col * n + col];
+      const long double f = A[(size_t)r * n + col];
       if (f == 0) continue;
       for (int q = 0; q < n; ++q) A[(size_t)r * n + q] -= f * A[(size_t)col * n + q];
       for (int q = 0; q <= E; ++q) X[(size_t)r * (E + 1) + q] -= f * X[(size_t)col * (E + 1) + q];
     }
-  const int u = k_out - k0;
-  const long double d = A[(size_t)u * n + u];
-  for (int j = 0; j < E; ++j) row[j] = X[(size_t)u * (E + 1) + j] / d;
-  *coup = X[(size_t)u * (E + 1) + E] / d;
+  }
+  W.assign((size_t)N * E, 0);
+  coup.assign(N, 0);
+  for (int k = 0; k < N; ++k) {
+    const int u = k - k0;
+    for (int j = 0; j < E; ++j) W[(size_t)k * E + j] = X[(size_t)u * (E + 1) + j];
+    coup[k] = X[(size_t)u * (E + 1) + E];
+  }
 }
-
-}  // namespace
 
 void build_biased_tables(const BiasedCoef &c, int N, int g, BiasedTables &T) {
   memset(&T, 0, sizeof(T));
@@ -85,14 +101,14 @@ void build_biased_tables(const BiasedCoef &c, int N, int g, BiasedTables &T) {
   }
   const int E = N + 2 * g;
   if (E > kMaxN + 16 || c.kc > N) return;   // refused later by the request checks
-  std::vector<long double> row(E);
-  long double coup;
+  std::vector<long double> W, coup;
   for (int side = 0; side < 2; ++side)
     for (int it = 0; it < 2; ++it) {
       const int sg = side == 0 ? 1 : -1;
-      biased_row(c, N, g, sg, it == 1, sg > 0 ? N - c.kc : c.kc - 1, row.data(), &coup);
-      for (int j = 0; j < E; ++j) T.hrow[side][it][j] = (double)row[j];
-      if (it == 1) T.hc[side] = (double)coup;
+      const int k = sg > 0 ? N - c.kc : c.kc - 1;
+      biased_operator(c, N, g, sg, it, W, coup);
+      for (int j = 0; j < E; ++j) T.hrow[side][it][j] = (double)W[(size_t)k * E + j];
+      if (it == 1) T.hc[side] = (double)coup[k];
     }
 }
 
@@ -395,8 +411,8 @@ cfd_status check_request(cfd_blocks_s *B, int nf, cfd_precision prec, int n_iter
     set_error("no biased scheme bound (cfd_scheme_set_biased before cfd_blocks_bind)");
     return CFD_ERR_ARG;
   }
-  if (prec != CFD_FP64_BANDED) {
-    set_error("biased path: only CFD_FP64_BANDED");
+  if (prec != CFD_FP64_BANDED && prec != CFD_TC_BF16_EXACT && prec != CFD_TC_BF16X3) {
+    set_error("biased path: CFD_FP64_BANDED, CFD_TC_BF16_EXACT or CFD_TC_BF16X3");
     return CFD_ERR_UNSUPPORTED;
   }
   if (n_iter < 0 || n_iter > 64) { set_error("biased path: n_iter out of range"); return CFD_ERR_ARG; }
@@ -478,9 +494,9 @@ cfd_status run_biased(cfd_blocks_s *B, const void *fields, int nf, const void *b
   return CFD_OK;
 }
 
-cfd_status check_work(cfd_blocks_s *B, int nf, int n_iter, void *work, size_t work_bytes) {
+cfd_status check_work(cfd_blocks_s *B, int nf, cfd_precision prec, int n_iter, void *work, size_t work_bytes) {
   size_t need = 0;
-  cfd_status s = cfd_biased_workspace(B, nf, n_iter, &need);
+  cfd_status s = cfd_biased_workspace(B, nf, prec, n_iter, &need);
   if (s != CFD_OK) return s;
   if (need > 0 && (!work || work_bytes < need)) {
     set_error("biased path: workspace too small (see cfd_biased_workspace)");
@@ -489,15 +505,74 @@ cfd_status check_work(cfd_blocks_s *B, int nf, int n_iter, void *work, size_t wo
   return CFD_OK;
 }
 
+// Upwind blend of the two biased derivatives of every axis (tensor-core path): one thread per
+// interior point of one (block, field); axes added in the order x, y, z.
+template <typename T>
+__global__ void k_advect_combine(const T *__restrict__ tmp, const T *__restrict__ beta, T *out,
+                                 const int *__restrict__ blocks, const long long *__restrict__ extpre,
+                                 const long long *__restrict__ intpre, int N, int g, int nf, int out_nops,
+                                 int out_opidx, int accum_all) {
+  const int n3 = N * N * N;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const int job = blockIdx.y;
+  const int lb = job / nf, q = job - lb * nf;
+  const int b = blocks[lb];
+  const int x = i % N, y = (i / N) % N, z = i / (N * N);
+  const int E = N + 2 * g;
+  const long long E3 = (long long)E * E * E;
+  const T *bt = beta + 3 * extpre[b] + ((long long)(z + g) * E + (y + g)) * E + (x + g);
+  const T *tp = tmp + (long long)nf * 6 * intpre[b] + (long long)q * 6 * n3 + i;
+  T *o = out + (long long)nf * out_nops * intpre[b] + ((long long)q * out_nops + out_opidx) * n3 + i;
+  double acc = accum_all ? static_cast<double>(*o) : 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T braw = __ldg(bt + c * E3);
+    const int sg = sign_bits(braw);
+    const double bb = static_cast<double>(braw);
+    const double t = sg == 1 ? bb * static_cast<double>(__ldg(tp + (2 * c) * n3))
+                             : (sg == 2 ? bb * static_cast<double>(__ldg(tp + (2 * c + 1) * n3)) : 0.0);
+    acc = (c == 0 && !accum_all) ? t : acc + t;
+  }
+  *o = static_cast<T>(acc);
+}
+
 }  // namespace
 
+cfd_status advect_combine(cfd_blocks_s *B, const void *tmp6, const void *beta, int nf, void *out, int out_nops,
+                          int out_opidx, bool accum_all, cudaStream_t st) {
+  for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
+    const int N = B->sizes[gi];
+    const int n3 = N * N * N;
+    dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)(B->groups[gi].size() * nf));
+    launch_begin(KF_BIASED, st);
+    if (B->dtype == CFD_F32)
+      k_advect_combine<float><<<grid, 256, 0, st>>>(static_cast<const float *>(tmp6), static_cast<const float *>(beta),
+                                                   static_cast<float *>(out), B->d_groups[gi], B->d_extpre,
+                                                   B->d_intpre, N, B->ng, nf, out_nops, out_opidx, accum_all);
+    else
+      k_advect_combine<double><<<grid, 256, 0, st>>>(static_cast<const double *>(tmp6),
+                                                     static_cast<const double *>(beta), static_cast<double *>(out),
+                                                     B->d_groups[gi], B->d_extpre, B->d_intpre, N, B->ng, nf,
+                                                     out_nops, out_opidx, accum_all);
+    launch_end(KF_BIASED, st);
+    cfd_status s = cuda_fail(cudaGetLastError(), "k_advect_combine launch");
+    if (s != CFD_OK) return s;
+  }
+  return CFD_OK;
+}
+
 cfd_status advect_accumulate(cfd_blocks_s *B, const void *field, const void *beta, void *out, int out_nops,
-                             int out_opidx, int n_iter, void *work, size_t work_bytes, cudaStream_t st) {
+                             int out_opidx, cfd_precision prec, int n_iter, void *work, size_t work_bytes,
+                             cudaStream_t st) {
   int win;
-  cfd_status s = check_request(B, 1, CFD_FP64_BANDED, n_iter, &win);
+  cfd_status s = check_request(B, 1, prec, n_iter, &win);
   if (s != CFD_OK) return s;
-  if ((s = check_work(B, 1, n_iter, work, work_bytes)) != CFD_OK) return s;
+  if ((s = check_work(B, 1, prec, n_iter, work, work_bytes)) != CFD_OK) return s;
   const int axes[3] = {2, 1, 0};
+  if (prec != CFD_FP64_BANDED)
+    return dense_biased(B, field, 1, beta, axes, 3, 2, prec, n_iter, out, out_nops, out_opidx, true, work,
+                        work_bytes, st);
   return run_biased(B, field, 1, beta, axes, 3, 2, n_iter, win, out, work, st, out_nops, out_opidx, true);
 }
 
@@ -541,8 +616,12 @@ cfd_status cfd_scheme_set_biased(cfd_scheme_t scheme, const cfd_biased_desc *d) 
   return CFD_OK;
 }
 
-cfd_status cfd_biased_workspace(cfd_blocks_t B, int nfields, int n_iter, size_t *bytes) {
+cfd_status cfd_biased_workspace(cfd_blocks_t B, int nfields, cfd_precision prec, int n_iter, size_t *bytes) {
   if (!B || nfields < 1 || n_iter < 0 || !bytes) { set_error("cfd_biased_workspace: bad argument"); return CFD_ERR_ARG; }
+  if (prec == CFD_TC_BF16_EXACT || prec == CFD_TC_BF16X3) {
+    *bytes = dense_biased_workspace(B, nfields, n_iter, true);
+    return CFD_OK;
+  }
   const size_t he = halo_elems(B, nfields, n_iter);
   *bytes = he ? 2 * align256(he * 8) + 256 : 0;
   return CFD_OK;
@@ -559,11 +638,14 @@ cfd_status cfd_apply_biased(cfd_blocks_t B, const void *fields, int nfields, uns
   int win;
   cfd_status s = check_request(B, nfields, prec, n_iter, &win);
   if (s != CFD_OK) return s;
-  if ((s = check_work(B, nfields, n_iter, work, work_bytes)) != CFD_OK) return s;
+  if ((s = check_work(B, nfields, prec, n_iter, work, work_bytes)) != CFD_OK) return s;
   int axes[3], n = 0;
   if (axis_mask & CFD_OP_DX) axes[n++] = 2;
   if (axis_mask & CFD_OP_DY) axes[n++] = 1;
   if (axis_mask & CFD_OP_DZ) axes[n++] = 0;
+  if (prec != CFD_FP64_BANDED)
+    return dense_biased(B, fields, nfields, nullptr, axes, n, side > 0 ? 0 : 1, prec, n_iter, out, 0, 0, false,
+                        work, work_bytes, (cudaStream_t)stream);
   return run_biased(B, fields, nfields, nullptr, axes, n, side > 0 ? 0 : 1, n_iter, win, out, work,
                     (cudaStream_t)stream);
 }
@@ -574,8 +656,11 @@ cfd_status cfd_advect(cfd_blocks_t B, const void *fields, int nfields, const voi
   int win;
   cfd_status s = check_request(B, nfields, prec, n_iter, &win);
   if (s != CFD_OK) return s;
-  if ((s = check_work(B, nfields, n_iter, work, work_bytes)) != CFD_OK) return s;
+  if ((s = check_work(B, nfields, prec, n_iter, work, work_bytes)) != CFD_OK) return s;
   const int axes[3] = {2, 1, 0};  // x, y, z
+  if (prec != CFD_FP64_BANDED)
+    return dense_biased(B, fields, nfields, beta, axes, 3, 2, prec, n_iter, out, 1, 0, false, work, work_bytes,
+                        (cudaStream_t)stream);
   return run_biased(B, fields, nfields, beta, axes, 3, 2, n_iter, win, out, work, (cudaStream_t)stream);
 }
 

@@ -70,6 +70,9 @@ struct BiasedParams {
 };
 
 void build_biased_tables(const BiasedCoef &c, int N, int g, BiasedTables &T);
+// dense form of a biased block system (kind 0 closed, 1 iterated, 2 cyclic), unscaled
+void biased_operator(const BiasedCoef &c, int N, int g, int side, int kind, std::vector<long double> &W,
+                     std::vector<long double> &coup);
 
 // Everything one pencil solve needs for one (block size N, degree d).
 // Passed to kernels by value.
@@ -169,9 +172,19 @@ void launch_begin(int family, cudaStream_t st);
 void launch_end(int family, cudaStream_t st);
 
 // biased.cu: out[slot out_opidx of out_nops per block] += sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f
-// for one FP64 field (FP64 banded; `work` as cfd_biased_workspace(B, 1, n_iter))
+// for one FP64 field (`work` as cfd_biased_workspace(B, 1, prec, n_iter))
 cfd_status advect_accumulate(cfd_blocks_s *B, const void *field, const void *beta, void *out, int out_nops,
-                             int out_opidx, int n_iter, void *work, size_t work_bytes, cudaStream_t st);
+                             int out_opidx, cfd_precision prec, int n_iter, void *work, size_t work_bytes,
+                             cudaStream_t st);
+// biased.cu: out slot = (accum_all ? out : 0) + sum_{i=x,y,z} beta^i (beta^i > 0 ? T[2i] : T[2i+1]),
+// T = [block][field][6][N^3] (both biased derivatives of every axis)
+cfd_status advect_combine(cfd_blocks_s *B, const void *tmp6, const void *beta, int nf, void *out, int out_nops,
+                          int out_opidx, bool accum_all, cudaStream_t st);
+// dense_tc.cu: the biased operators on the tensor cores
+size_t dense_biased_workspace(const cfd_blocks_s *B, int nf, int n_iter, bool advect);
+cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void *beta, const int *axes, int naxes,
+                        int mode, cfd_precision prec, int n_iter, void *out, int out_nops, int out_opidx,
+                        bool accum_all, void *work, size_t work_bytes, cudaStream_t st);
 
 // kernels (banded.cu)
 cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nfields, cudaStream_t st);

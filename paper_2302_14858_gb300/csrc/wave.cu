@@ -343,7 +343,7 @@ cfd_status lsrk_impl(const char *who, cfd_blocks_s *B, void *phi, void *K, const
   cfd_status s = wave_layout(B, prec, n_iter, L);
   if (s != CFD_OK) return s;
   size_t bws = 0;
-  if (beta && (s = cfd_biased_workspace(B, 1, n_iter, &bws)) != CFD_OK) return s;
+  if (beta && (s = cfd_biased_workspace(B, 1, prec, n_iter, &bws)) != CFD_OK) return s;
   const size_t need = al(L.in * 8) * 2 + al(3 * L.in * 8) + al(L.apply) + bws + 256;
   if (work_bytes < need) return fail(CFD_ERR_ARG, "workspace too small");
   char *base = (char *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
@@ -409,8 +409,8 @@ cfd_status lsrk_impl(const char *who, cfd_blocks_s *B, void *phi, void *K, const
     }
     if (beta) {
       // F_Phi (slot 1) += beta . grad Phi, F_K (slot 0) += beta . grad K, upwinded
-      if ((s = advect_accumulate(B, phi, beta, lap, 3, 1, n_iter, bw, bws, st)) != CFD_OK) return s;
-      if ((s = advect_accumulate(B, K, beta, lap, 3, 0, n_iter, bw, bws, st)) != CFD_OK) return s;
+      if ((s = advect_accumulate(B, phi, beta, lap, 3, 1, prec, n_iter, bw, bws, st)) != CFD_OK) return s;
+      if ((s = advect_accumulate(B, K, beta, lap, 3, 0, prec, n_iter, bw, bws, st)) != CFD_OK) return s;
     }
     for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
       const int N = B->sizes[gi];
@@ -459,7 +459,7 @@ extern "C" cfd_status cfd_shifted_wave_workspace(cfd_blocks_t B, cfd_precision p
   cfd_status s = wave_layout(B, prec, n_iter, L);
   if (s != CFD_OK) return s;
   size_t bws = 0;
-  if ((s = cfd_biased_workspace(B, 1, n_iter, &bws)) != CFD_OK) return s;
+  if ((s = cfd_biased_workspace(B, 1, prec, n_iter, &bws)) != CFD_OK) return s;
   *bytes = al(L.in * 8) * 2 + al(3 * L.in * 8) + al(L.apply) + bws + 256;
   return CFD_OK;
 }

@@ -45,32 +45,60 @@ def bind(lib, name, mesh, g, dtype):
     return lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, dtype)
 
 
-def run_biased(lib, torch, blocks, buf, nf, mask, side, n_iter, dtype=np.float64):
+TOL_TC = 1e-7       # exact digit slices on the tensor cores (the centred path's contract)
+
+
+def run_biased(lib, torch, blocks, buf, nf, mask, side, n_iter, dtype=np.float64, prec=0):
     dev = torch.device("cuda", 0)
     fields = torch.from_numpy(np.ascontiguousarray(buf.astype(dtype))).to(dev)
     nops = bin(mask).count("1")
     nint = sum(int(n) ** 3 for n in blocks.block_n)
     out = torch.zeros(nint * nf * nops, dtype=fields.dtype, device=dev)
-    ws = lib.cfd_biased_workspace(blocks, nf, n_iter)
+    ws = lib.cfd_biased_workspace(blocks, nf, prec, n_iter)
     work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
-    lib.cfd_apply_biased(blocks, fields, nf, mask, side, lib.CFD_FP64_BANDED, n_iter, out, work)
+    lib.cfd_apply_biased(blocks, fields, nf, mask, side, prec, n_iter, out, work)
     lib.cfd_sync_status(blocks)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
 
-def check_biased(lib, torch, name, NM, N, g, side, n_iter, nf=2, seed=11):
+def check_biased(lib, torch, name, NM, N, g, side, n_iter, nf=2, seed=11, prec=0):
     fields = case_fields(seed, nf)
     mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
     blocks = bind(lib, name, mesh, g, lib.CFD_F64)
-    got = run_biased(lib, torch, blocks, buf, nf, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, n_iter)
+    got = run_biased(lib, torch, blocks, buf, nf, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, n_iter,
+                     prec=prec)
     got = got.reshape(mesh.nblocks, nf, 3, N, N, N)
     b = biased_of(name)
+    tol = TOL64 if prec == 0 else TOL_TC
     for q in range(nf):
         want = B.biased_uniform(exts[q], b, side, (dx, dx, dx), N, g, AXES, n_iter)
         for i, c in enumerate(AXES):
             w = want[c].reshape(mesh.nblocks, N, N, N)
-            assert rel_max(got[:, q, i], w) < TOL64, (name, side, n_iter, q, c, rel_max(got[:, q, i], w))
+            assert rel_max(got[:, q, i], w) < tol, (name, side, n_iter, q, c, rel_max(got[:, q, i], w))
+
+
+@pytest.mark.parametrize("name", ["X2_d1", "Q1034_1_d1"])
+@pytest.mark.parametrize("side", [1, -1])
+@pytest.mark.parametrize("NM,N,n_iter", [(64, 16, 0), (64, 16, 1), (64, 32, 1), (64, 16, 2)])
+def test_biased_parity_tensor_cores(lib, torch, name, side, NM, N, n_iter):
+    """The dense biased operators (closed, iterated with one-sided halo columns) on the tensor
+    cores, exact digit slices."""
+    check_biased(lib, torch, name, NM, N, 4, side, n_iter, prec=2)
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_biased_tensor_cores_bf16x3(lib, torch, side):
+    """BF16 hi/lo (3 products) on the same operators: the lower-precision measured mode
+    (5e-4 measured here; bound 5e-3, as the centred path keeps this mode's bound separate from
+    the FP64-grade contract)."""
+    NM, N, g = 64, 16, 4
+    fields = case_fields(11, 1)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    blocks = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX, side, 1, prec=1).reshape(mesh.nblocks, N, N, N)
+    want = B.biased_uniform(exts[0], biased_of("X2_d1"), side, (dx, dx, dx), N, g, ("x",), 1)["x"]
+    assert rel_max(got, want.reshape(mesh.nblocks, N, N, N)) < 5e-3
 
 
 @pytest.mark.parametrize("name", ["X1_d1", "X2_d1", "Q1034_1_d1"])
@@ -102,13 +130,15 @@ def test_single_block_is_the_cyclic_scheme(lib, torch, side):
     fields = case_fields(5, 1)
     mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
     blocks = bind(lib, "Q1034_1_d1", mesh, g, lib.CFD_F64)
-    got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, 2)
-    got = got.reshape(3, N, N, N)
     b = biased_of("Q1034_1_d1")
     fg = exts[0][0, 0, 0][g:g + N, g:g + N, g:g + N]
-    for i, ax in enumerate((2, 1, 0)):
-        want = np.moveaxis(B.global_periodic(np.moveaxis(fg, ax, 0), b, side, dx), 0, ax)
-        assert rel_max(got[i], want) < TOL64
+    for prec, tol in ((0, TOL64), (2, TOL_TC)):
+        got = run_biased(lib, torch, blocks, buf, 1, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, 2,
+                         prec=prec)
+        got = got.reshape(3, N, N, N)
+        for i, ax in enumerate((2, 1, 0)):
+            want = np.moveaxis(B.global_periodic(np.moveaxis(fg, ax, 0), b, side, dx), 0, ax)
+            assert rel_max(got[i], want) < tol, (prec, i)
 
 
 def test_iteration_reaches_the_global_scheme(lib, torch):
@@ -157,7 +187,8 @@ def shift_fields():
 @pytest.mark.parametrize("name,g", [("X2_d1", 4), ("Q1034_1_d1", 4)])
 @pytest.mark.parametrize("n_iter", [0, 1, 2])
 @pytest.mark.parametrize("shift", ["mixed", "one_sign"])
-def test_advect_parity(lib, torch, name, g, n_iter, shift):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_advect_parity(lib, torch, name, g, n_iter, shift, prec):
     """out = sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f on 4^3 blocks of 16^3, 3 fields.
     "one_sign": beta^x > 0, beta^y = 0, beta^z < 0 everywhere (pencils that need one side, or none)."""
     NM, N, nf = 64, 16, 3
@@ -172,9 +203,9 @@ def test_advect_parity(lib, torch, name, g, n_iter, shift):
     f_t = torch.from_numpy(buf).to(dev)
     b_t = torch.from_numpy(bbuf).to(dev)
     out = torch.zeros(mesh.nblocks * nf * N ** 3, dtype=torch.float64, device=dev)
-    ws = lib.cfd_biased_workspace(blocks, nf, n_iter)
+    ws = lib.cfd_biased_workspace(blocks, nf, prec, n_iter)
     work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
-    lib.cfd_advect(blocks, f_t, nf, b_t, lib.CFD_FP64_BANDED, n_iter, out, work)
+    lib.cfd_advect(blocks, f_t, nf, b_t, prec, n_iter, out, work)
     lib.cfd_sync_status(blocks)
     got = out.cpu().numpy().reshape(mesh.nblocks, nf, N, N, N)
     I = slice(g, g + N)
@@ -182,7 +213,7 @@ def test_advect_parity(lib, torch, name, g, n_iter, shift):
     b = biased_of(name)
     for q in range(nf):
         want = B.advect_uniform(exts[q], beta, b, (dx, dx, dx), N, g, n_iter).reshape(mesh.nblocks, N, N, N)
-        assert rel_max(got[:, q], want) < TOL64
+        assert rel_max(got[:, q], want) < (TOL64 if prec == 0 else TOL_TC)
 
 
 def test_rejections(lib, torch):
@@ -199,9 +230,12 @@ def test_rejections(lib, torch):
         lib.cfd_apply_biased(B0, f_t, 1, lib.CFD_OP_DX, 1, 0, 0, out)
     assert e.value.status == lib.CFD_ERR_ARG
     blocks = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
-    with pytest.raises(lib.CfdError) as e:                       # tensor cores: not on this path
-        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 1, lib.CFD_TC_BF16_EXACT, 0, out)
+    with pytest.raises(lib.CfdError) as e:                       # TF32 is not built
+        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 1, lib.CFD_TC_TF32, 0, out)
     assert e.value.status == lib.CFD_ERR_UNSUPPORTED
+    with pytest.raises(lib.CfdError) as e:                       # tensor cores need their workspace
+        lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 1, lib.CFD_TC_BF16_EXACT, 0, out, None)
+    assert e.value.status == lib.CFD_ERR_ARG
     with pytest.raises(lib.CfdError) as e:                       # side must be +-1
         lib.cfd_apply_biased(blocks, f_t, 1, lib.CFD_OP_DX, 0, 0, 0, out)
     assert e.value.status == lib.CFD_ERR_ARG
