@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gpoint-ops/s: split-BF16 TC CFD vs FP64 banded solve, err ≤1e-6 vs FP64"
 ADVECT_METRIC = "Gpoint-ops/s: upwinded shift advection (biased CCU X_2 pencil solves)"
+ADV2D_METRIC = "Gpoint-ops/s: 2D advection, upwinded CCU X_2, 2S RK + KO"
 L2_BYTES = 129 * 2 ** 20
 FP64_NOMINAL_GFLOPS = 1250.0      # GB300 FP64 (non-tensor) nominal, profiling recipe table
 
@@ -55,6 +56,11 @@ WORKLOADS = {
     # known: each mode's frequency is |k| - beta.k)
     "shiftwave256_b32_x2_lsrk": dict(kind="wave", NM=256, N=32, nf=2, dtype="f64", n_iter=1, modes=8, kmax=20.0,
                                      shift=(0.3, -0.2, 0.1)),
+    # 2D advection u_t + c . grad u = 0 (Sec. "Two dimensional advection"): 192^2 as 12 x 12 blocks of 16^2
+    # (one 16-point block thick in z), the paper's initial profile g(x) h(y), direction 30 degrees,
+    # upwinded CCU X_2, one iteration, 2S RK + Kreiss-Oliger (sigma 0.04, r = 4), dt = dx / 10
+    "adv2d192_b16_x2_lsrk": dict(kind="adv2d", NM=192, N=16, nf=1, dtype="f64", n_iter=1, angle_deg=30.0,
+                                 cfl=0.1),
     # upwinded shift advection sum_i beta^i d_i f (Eq. biasderapproxadv) with the CCU X_2^-
     # scheme and its mirror (Tab. ccux_deg_one_col), 256^3 as 512 blocks of 32^3, 4 FP64 fields,
     # one iteration of Eq. iter_left_X
@@ -321,6 +327,31 @@ def cpu_baseline(spec, seconds=12.0):
         el = time.perf_counter() - t0
         return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
                 "sample": f"oracle wave_rk4_step, {NS}^3 as {(NS // N) ** 3} blocks of {N}^3, {reps} RK4 steps"}
+    if spec["kind"] == "adv2d":
+        from oracle import biased as BO
+        from oracle import timestep as TS
+        d = biased_desc()
+        bs = BO.Biased(d["a"], d["lo"], tuple(d["rhs"]), d["c_sup"], d["c_lo"], tuple(d["closure"]), d["kc"])
+        NS, N = 64, spec["N"]
+        dx = 2 * np.pi / spec["NM"]
+        x = (np.arange(NS) + 0.5) * dx
+        z = (np.arange(N) + 0.5) * dx
+        Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+        u = adv2d_profile(X, Y)
+        phi = math.radians(spec["angle_deg"])
+        beta = [np.full_like(X, -math.cos(phi)), np.full_like(X, -math.sin(phi)), 0 * X]
+        coef = TS.lsrk2s_rk4_float()
+        units, reps = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            u = TS.advect_lsrk_step(u, beta, spec["cfl"] * dx, coef, bs, (dx, dx, dx), N, g, spec["n_iter"], 0.04, 4)
+            units += NS * NS * N * 4
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        el = time.perf_counter() - t0
+        return {"value": units / el / 1e9, "unit": "Gpoint-ops/s", "cores": 1, "kind": "oracle",
+                "sample": f"oracle advect_lsrk_step, {NS}x{NS}x{N} as {(NS // N) ** 2} blocks of {N}^3, {reps} steps"}
     if spec["kind"] == "advect":
         from oracle import biased as BO
         d = biased_desc()
@@ -472,6 +503,8 @@ def main():
         return run_wave(args, spec)
     if spec["kind"] == "advect":
         return run_advect(args, spec)
+    if spec["kind"] == "adv2d":
+        return run_adv2d(args, spec)
 
     import torch
     if world > 1:
@@ -847,6 +880,124 @@ def run_advect(args, spec):
         torch.distributed.destroy_process_group()
 
 
+def adv2d_profile(x, y):
+    """u(x, y) = g(x) h(y) of Sec. "Two dimensional advection": g of Eq. test_grid_conv_g with
+    (A, x0, N1, S) = (5/100, 2/10, 2, 1), h of Eq. test_grid_conv_h with
+    (S, x0, c1, c2, N1, N2, phi_S) = (15/10, pi, 12/10, -1, 2, 7, 1); works on numpy or torch."""
+    lib = np if isinstance(x, np.ndarray) else __import__("torch")
+    gx = 0.05 * lib.exp(-1.0 * lib.sin(2 * (x - 0.2)))
+    hy = lib.exp(-1.5 * (y - math.pi) ** 2) * (1.2 * lib.sin(7 * y) - lib.cos(7 * y)) + lib.sin(2 * y - 1.0)
+    return gx * hy
+
+
+def run_adv2d(args, spec):
+    """2D advection on the GPU: steps/s, Gpoint-ops/s (points x 4 stages, one advective term each)
+    and the max error against the exactly translated profile after the timed steps."""
+    import torch
+    from paper_2302_14858_gb300 import cfd, workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    NM, N, g = spec["NM"], spec["N"], 4
+    nb = NM // N
+    mesh = W.periodic_box_mesh(nb, nb, 1, N, g)
+    E = N + 2 * g
+    dx = 2 * math.pi / NM
+    phi = math.radians(spec["angle_deg"])
+    c = (math.cos(phi), math.sin(phi))
+    dt = spec["cfl"] * dx
+    coef = ([0.0, 0.068841064670197562, 0.62754761399692844, -0.59911219706265022],
+            [1.0, 0.81058824734452378, 1.3891900984667538, 1.2610225117075399],
+            [1.2299693289723146, 0.079894519849001553, 0.93225854169045408, 0.45482163406909008],
+            [1.0, 0.14874467817694941, -0.88063710498437737, 1.0])
+
+    def field(t):
+        # interior and ghosts of every block from the translated profile, periodic in x and y
+        out = torch.empty((mesh.nblocks, E, E, E), dtype=torch.float64, device=dev)
+        loc = (torch.arange(-g, N + g, dtype=torch.float64, device=dev) + 0.5)
+        for b in range(mesh.nblocks):
+            xs = (mesh.origin[b, 0] + loc) * dx
+            ys = (mesh.origin[b, 1] + loc) * dx
+            Y, X = torch.meshgrid(ys, xs, indexing="ij")
+            u = adv2d_profile(torch.remainder(X - c[0] * t, 2 * math.pi), torch.remainder(Y - c[1] * t, 2 * math.pi))
+            out[b] = u[None, :, :].expand(E, E, E)
+        return out.reshape(-1)
+
+    u0 = field(0.0)
+    u = u0.clone()
+    beta = torch.empty((mesh.nblocks, 3, E, E, E), dtype=torch.float64, device=dev)
+    beta[:, 0] = -c[0]
+    beta[:, 1] = -c[1]
+    beta[:, 2] = 0.0
+    beta = beta.reshape(-1)
+    d1, _ = scheme_descs()
+    scheme = cfd.cfd_scheme_create(d1, None)
+    cfd.cfd_scheme_set_biased(scheme, biased_desc())
+    blocks = cfd.cfd_blocks_bind(scheme, mesh.n, mesh.dx, mesh.neighbors, g, cfd.CFD_F64)
+    stream = torch.cuda.current_stream(dev)
+    n_iter = spec["n_iter"]
+    sigma, r = 0.04, 4
+
+    def run(prec, steps):
+        work = torch.empty(cfd.cfd_advect_lsrk_workspace(blocks, 1, prec, n_iter), dtype=torch.uint8, device=dev)
+        step = lambda: cfd.cfd_advect_lsrk_step(blocks, u, 1, beta, dt, coef, sigma, r, prec, n_iter, work, stream)
+        u.copy_(u0)
+        for _ in range(args.warmup):
+            step()
+        u.copy_(u0)
+        torch.cuda.synchronize()
+        ms = timed(step, steps, stream, torch)
+        cfd.cfd_sync_status(blocks, stream)
+        exact = field(steps * dt).view(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
+        got = u.view(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
+        err = float((got - exact).abs().max())
+        return ms, err
+
+    prec = PREC[args.prec]
+    clocks = ClockSampler(local)
+    launches0 = cfd.cfd_kernel_launches()
+    clocks.start()
+    time.sleep(0.3)
+    ms, err = run(prec, args.steps)
+    clk = clocks.stop()
+    launches = cfd.cfd_kernel_launches() - launches0
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    units = NM * NM * N * 4
+    compare = None
+    if not args.no_compare and prec != PREC["fp64_banded"]:
+        ms64, err64 = run(PREC["fp64_banded"], args.steps)
+        compare = {"fp64_banded": {"steps_per_s": round(1e3 / ms64, 3), "ms_per_step": round(ms64, 4),
+                                   "max_err_vs_exact": err64}, "speedup_vs_fp64_banded": round(ms64 / ms, 3)}
+    cpu = cpu_baseline(spec) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    if rank == 0:
+        line = {
+            "metric": ADV2D_METRIC, "value":
+                round(units * world / (ms * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (the paper's analytic profile g(x) h(y))",
+            "config": {"workload": args.workload, "path": args.prec, "n_iter": n_iter, "blocks": mesh.nblocks,
+                       "grid": [NM, NM], "block": N, "angle_deg": spec["angle_deg"], "cfl": spec["cfl"],
+                       "ko": {"sigma": sigma, "r": r}, "parallelism": f"replicas x{world}"},
+            "steps_per_s": round(1e3 / ms * world, 3), "t_final": args.steps * dt, "max_err_vs_exact": err,
+            "compare": compare, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_wave(args, spec):
     """The RK4 wave driver: Gpoint-ops/s (3 second-derivative ops x points x 4 stages per step),
     steps/s, and the phase and amplitude errors of every plane-wave mode against the exact
@@ -1007,7 +1158,8 @@ def run_reference(args, spec, rank):
         vals.append(cpu_baseline(spec, seconds=2.0))
     el = time.perf_counter() - t0
     v = statistics.median(r["value"] for r in vals)
-    line = {"metric": ADVECT_METRIC if spec["kind"] == "advect" else METRIC, "value": round(v, 6),
+    metric = {"advect": ADVECT_METRIC, "adv2d": ADV2D_METRIC}.get(spec["kind"], METRIC)
+    line = {"metric": metric, "value": round(v, 6),
             "unit": "Gpoint-ops/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

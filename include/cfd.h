@@ -324,13 +324,17 @@ cfd_status cfd_apply_biased(cfd_blocks_t blocks, const void *fields, int nfields
                             void *stream);
 
 /*
- * Upwinded shift advection (Eq. biasderapproxadv with the advection speed
- * replaced by the pointwise shift, Sec. "Z4c: system description"): for every
- * block and field
- *     out = sum_{i = x, y, z} beta^i_+ D_i[S_+] f + beta^i_- D_i[S_-] f,
+ * Upwinded shift-advection term beta^i d_i f as it appears on a right-hand
+ * side (u_t = beta^i d_i u + ..., Sec. "Z4c: system description"): it
+ * transports with velocity c = -beta^i, and Eq. biasderapproxadv takes the
+ * scheme with Im eta~ <= 0 (S_+, left-biased) where c > 0.  For every block
+ * and field
+ *     out = sum_{i = x, y, z} beta^i_+ D_i[S_-] f + beta^i_- D_i[S_+] f,
  *     beta_+- = (beta +- |beta|) / 2,
- * i.e. beta^i d_i f with the left-biased scheme where beta^i > 0 and the
- * right-biased one where beta^i < 0.  `beta` holds three fields (beta^x,
+ * i.e. the right-biased scheme where beta^i > 0 and the left-biased one
+ * where beta^i < 0 (for u_t + c . grad u = 0 pass beta = -c).  With this
+ * choice the semi-discrete operator has no growing mode; the opposite one
+ * is anti-dissipative.  `beta` holds three fields (beta^x,
  * beta^y, beta^z) in the field layout (ghosts unused); `out` one N^3 array
  * per block and field.  Arithmetic as cfd_apply_biased; the three axis terms
  * are added in the order x, y, z (the tensor-core form writes both biased
@@ -360,6 +364,26 @@ cfd_status cfd_shifted_wave_workspace(cfd_blocks_t blocks, cfd_precision prec, i
 cfd_status cfd_shifted_wave_lsrk_step(cfd_blocks_t blocks, void *phi, void *K, const void *beta, double dt,
                                       const cfd_lsrk_desc *rk, double sigma, int ko_r, cfd_precision prec,
                                       int n_iter, void *work, size_t work_bytes, void *stream);
+
+/* Device workspace of cfd_advect_lsrk_step (bytes). */
+cfd_status cfd_advect_lsrk_workspace(cfd_blocks_t blocks, int nfields, cfd_precision prec, int n_iter,
+                                     size_t *bytes);
+
+/*
+ * One step of the 2S method (cfd_lsrk_desc) for the advection equation of
+ * every field, u_t = beta^i d_i u + sum_i Q_i[u] (Eq. tr2pde of Sec. "Two
+ * dimensional advection" with c = -beta, and the shift-advection term of
+ * Sec. "Z4c: system description"): the advective term is cfd_advect (upwinded
+ * biased operators, arithmetic `prec`), Q_i the Kreiss-Oliger term of
+ * cfd_wave_lsrk_step (FP64; none when sigma = 0).  `u`: nfields fields in the
+ * field layout, advanced in place (ghosts are exchanged every stage); `beta`:
+ * three fields as for cfd_advect, constant during the step.  Needs a biased
+ * scheme (cfd_scheme_set_biased).  FP64 fields, every ghost region with a
+ * neighbour.  Errors as cfd_advect plus CFD_ERR_ARG for the coefficients.
+ */
+cfd_status cfd_advect_lsrk_step(cfd_blocks_t blocks, void *u, int nfields, const void *beta, double dt,
+                                const cfd_lsrk_desc *rk, double sigma, int ko_r, cfd_precision prec, int n_iter,
+                                void *work, size_t work_bytes, void *stream);
 
 /* Wait for `stream`, then read and clear the device status word of the
  * handle: CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_DEVICE_ASSERT. */

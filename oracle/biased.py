@@ -45,14 +45,20 @@ the interior scheme (right-biased: k^c_+ = k*_+ + kc, rows k*_- .. k^c_+ - 1).
 Each system is assembled as a dense N x N (or (N+kc) x (N+kc)) matrix and
 solved with the library dense solver.
 
-Upwinding (Eq. biasderapproxadv, Sec. "Z4c: system description"): the
-advective term beta^i d_i f is replaced pointwise by
-    beta^i_+ D_i[S_+] f + beta^i_- D_i[S_-] f,   beta_+- = (beta +- |beta|)/2,
-where S_+ is the scheme with Im eta~ <= 0 (here the left-biased scheme) and
-S_- its mirror.  Reading: as printed the weights (|c| -+ c)/2 multiply D
-without the sign of c, which does not reduce to c D for c < 0; the reading
-is the standard split c_+ D[S_+] + c_- D[S_-], equal to c D[S_+] for c > 0
-and c D[S_-] for c < 0.
+Upwinding (Eq. biasderapproxadv, Sec. "Two dimensional advection" and Sec.
+"Z4c: system description"): in u_t + c u_x = 0 the term c D u takes S_+ (the
+scheme with Im eta~ <= 0, here the left-biased one) where c > 0 and S_- (its
+mirror) where c < 0, so that the semi-discrete operator -c D has no growing
+modes.  Reading: as printed the weights (|c| -+ c)/2 multiply D without the sign
+of c, which does not reduce to c D for c < 0; the reading is the split
+c_+ D[S_+] + c_- D[S_-], c_+- = (c +- |c|)/2.  A shift-advection term
+beta^i d_i u on the right-hand side (u_t = beta^i d_i u + ...) transports with
+velocity c = -beta^i, so it becomes
+    beta^i_- D_i[S_+] u + beta^i_+ D_i[S_-] u,   beta_+- = (beta +- |beta|)/2:
+the right-biased scheme where beta^i > 0 and the left-biased one where
+beta^i < 0.  (Taking c = +beta^i instead makes the operator anti-dissipative:
+the pin below shows eigenvalues with Re > 0, and an evolution grows without
+bound.)
 """
 from __future__ import annotations
 
@@ -401,8 +407,8 @@ def biased_uniform(ext: np.ndarray, b: Biased, side: int, dx3: Sequence[float], 
 
 def advect_uniform(ext: np.ndarray, beta: Sequence[np.ndarray], b: Biased, dx3: Sequence[float],
                    N: int, g: int, n_iter: int = 0) -> np.ndarray:
-    """Upwinded beta^i d_i f (Eq. biasderapproxadv with the pointwise shift):
-    sum over i = x, y, z (in that order) of beta^i_+ D_i[S_+] f + beta^i_- D_i[S_-] f.
+    """Upwinded right-hand-side term beta^i d_i f (Eq. biasderapproxadv with c = -beta^i pointwise):
+    sum over i = x, y, z (in that order) of beta^i_- D_i[S_+] f + beta^i_+ D_i[S_-] f.
     ``beta`` = (beta^x, beta^y, beta^z), each (nbz, nby, nbx, N, N, N) interior."""
     dp = biased_uniform(ext, b, +1, dx3, N, g, ("x", "y", "z"), n_iter)
     dm = biased_uniform(ext, b, -1, dx3, N, g, ("x", "y", "z"), n_iter)
@@ -410,6 +416,6 @@ def advect_uniform(ext: np.ndarray, beta: Sequence[np.ndarray], b: Biased, dx3: 
     for c, bc in zip(("x", "y", "z"), beta):
         bp = 0.5 * (bc + np.abs(bc))
         bm = 0.5 * (bc - np.abs(bc))
-        term = bp * dp[c] + bm * dm[c]
+        term = bm * dp[c] + bp * dm[c]
         out = term if out is None else out + term
     return out

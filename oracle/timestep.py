@@ -256,3 +256,25 @@ def exp_integrate(L: np.ndarray, U0: np.ndarray, t: float) -> np.ndarray:
     import scipy.linalg as sl
     return sl.expm(t * L) @ U0
 
+
+# ---------------------------------------------------------------------------
+# Advection with upwinded biased operators (Eq. tr2pde with c = -beta)
+# ---------------------------------------------------------------------------
+
+
+def advect_rhs(u, beta, b, dx3, N, g, n_iter, sigma, r):
+    """F = beta . grad u (upwinded, ``oracle.biased.advect_uniform``) + sum_i Q_i[u] on a global
+    periodic (z, y, x) array; ``beta`` = (beta^x, beta^y, beta^z) global arrays."""
+    from oracle import biased as B
+    from oracle import cfd as C
+    bb = [C.global_to_blocks(v, N) for v in beta]
+    F = C.blocks_to_global(B.advect_uniform(C.ghost_fill_3d(u, N, g), bb, b, dx3, N, g, n_iter))
+    if sigma > 0:
+        F = F + ko_dissipation(u, r, sigma, dx3)
+    return F
+
+
+def advect_lsrk_step(u, beta, dt, coef, b, dx3, N, g, n_iter=0, sigma=0.0, r=4):
+    """One 2S step of u_t = beta . grad u + sum_i Q_i[u]."""
+    return lsrk2s_step((u,), dt, coef, lambda st: (advect_rhs(st[0], beta, b, dx3, N, g, n_iter, sigma, r),))[0]
+

@@ -44,7 +44,8 @@ EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd
            "cfd_sync_status", "cfd_last_error",
            "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static",
            "cfd_scheme_set_biased", "cfd_biased_workspace", "cfd_apply_biased", "cfd_advect",
-           "cfd_shifted_wave_workspace", "cfd_shifted_wave_lsrk_step")
+           "cfd_shifted_wave_workspace", "cfd_shifted_wave_lsrk_step", "cfd_advect_lsrk_workspace",
+           "cfd_advect_lsrk_step")
 KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4, "biased": 5}
 
 
@@ -117,6 +118,11 @@ _lib.cfd_shifted_wave_workspace.restype = c_int
 _lib.cfd_shifted_wave_lsrk_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, POINTER(LsrkDesc),
                                             c_double, c_int, c_int, c_int, c_void_p, c_size_t, c_void_p]
 _lib.cfd_shifted_wave_lsrk_step.restype = c_int
+_lib.cfd_advect_lsrk_workspace.argtypes = [c_void_p, c_int, c_int, c_int, POINTER(c_size_t)]
+_lib.cfd_advect_lsrk_workspace.restype = c_int
+_lib.cfd_advect_lsrk_step.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_double, POINTER(LsrkDesc), c_double,
+                                      c_int, c_int, c_int, c_void_p, c_size_t, c_void_p]
+_lib.cfd_advect_lsrk_step.restype = c_int
 _lib.cfd_sync_status.argtypes = [c_void_p, c_void_p]
 _lib.cfd_sync_status.restype = c_int
 _lib.cfd_kernel_launches.argtypes = []
@@ -336,6 +342,26 @@ def cfd_shifted_wave_lsrk_step(blocks: Blocks, phi, K, beta, dt: float, coef, si
     _check(_lib.cfd_shifted_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), _ptr(beta), float(dt),
                                            ctypes.byref(desc), float(sigma), int(ko_r), prec, n_iter, _ptr(work),
                                            _nbytes(work), _stream(stream)))
+
+
+def cfd_advect_lsrk_workspace(blocks: Blocks, nfields: int, prec: int, n_iter: int) -> int:
+    n = c_size_t()
+    _check(_lib.cfd_advect_lsrk_workspace(blocks.handle, nfields, prec, n_iter, ctypes.byref(n)))
+    return n.value
+
+
+def cfd_advect_lsrk_step(blocks: Blocks, u, nfields: int, beta, dt: float, coef, sigma: float, ko_r: int, prec: int,
+                         n_iter: int, work, stream=None):
+    """2S step of u_t = beta . grad u (+ Kreiss-Oliger) for nfields fields; coef = (gamma1, gamma2, beta, delta)."""
+    g1, g2, be, de = (list(map(float, c)) for c in coef)
+    m = len(be)
+    if not (len(g1) == len(g2) == len(de) == m):
+        raise ValueError("the four coefficient sequences need the same length")
+    arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
+    desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
+    _check(_lib.cfd_advect_lsrk_step(blocks.handle, _ptr(u), nfields, _ptr(beta), float(dt), ctypes.byref(desc),
+                                     float(sigma), int(ko_r), prec, n_iter, _ptr(work), _nbytes(work),
+                                     _stream(stream)))
 
 
 def cfd_sync_status(blocks: Blocks, stream=None):

@@ -8,8 +8,9 @@
 // recurrences: left-biased rows run k = 0..N-1 (a 2x2 solve couples the closure
 // row k*_- with row 1), right-biased rows run k = N-1..0.  In advect mode the
 // right-biased derivative is kept in registers and combined with the left-biased
-// one as it is produced, so one pass over the pencil yields
-// beta_+ D[S+] f + beta_- D[S-] f for that axis.
+// one as it is produced, so one pass over the pencil yields the upwinded right-hand-side term
+// beta d f = beta_+ D[S-] f + beta_- D[S+] f for that axis (transport velocity -beta: the
+// right-biased scheme where beta > 0, the left-biased one where beta < 0).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -240,8 +241,8 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
     int any = 0;
 #pragma unroll
     for (int k = 0; k < NT; ++k) any |= sign_bits(__ldg(bet + k * sa));
-    need_p = (any & 1) != 0;
-    need_m = (any & 2) != 0;
+    need_p = (any & 2) != 0;   // beta < 0 somewhere: left-biased
+    need_m = (any & 1) != 0;   // beta > 0 somewhere: right-biased
   }
 
   // ---- right-biased derivative (S-), rows k = N-1 .. 0, kept in registers
@@ -293,11 +294,11 @@ __global__ void __launch_bounds__(128) k_biased(const BiasedParams P, const Bias
     } else if (P.mode == 1) {
       v = dm[k];
     } else {
-      // beta_+ dp + beta_- dm: beta dp where beta > 0, beta dm where beta < 0, 0 where beta = 0
+      // beta_+ dm + beta_- dp: beta dm where beta > 0, beta dp where beta < 0, 0 where beta = 0
       const T braw = __ldg(bet + k * sa);
       const int sg = sign_bits(braw);
       const double bb = static_cast<double>(braw);
-      v = sg == 1 ? bb * dp : (sg == 2 ? bb * dm[k] : 0.0);
+      v = sg == 1 ? bb * dm[k] : (sg == 2 ? bb * dp : 0.0);
     }
     if (P.accum) v = static_cast<double>(o[k * oa]) + v;
     o[k * oa] = static_cast<T>(v);
@@ -530,8 +531,9 @@ __global__ void k_advect_combine(const T *__restrict__ tmp, const T *__restrict_
     const T braw = __ldg(bt + c * E3);
     const int sg = sign_bits(braw);
     const double bb = static_cast<double>(braw);
-    const double t = sg == 1 ? bb * static_cast<double>(__ldg(tp + (2 * c) * n3))
-                             : (sg == 2 ? bb * static_cast<double>(__ldg(tp + (2 * c + 1) * n3)) : 0.0);
+    // beta > 0: the right-biased derivative (slot 2c+1); beta < 0: the left-biased one (slot 2c)
+    const double t = sg == 1 ? bb * static_cast<double>(__ldg(tp + (2 * c + 1) * n3))
+                             : (sg == 2 ? bb * static_cast<double>(__ldg(tp + (2 * c) * n3)) : 0.0);
     acc = (c == 0 && !accum_all) ? t : acc + t;
   }
   *o = static_cast<T>(acc);
@@ -562,18 +564,18 @@ cfd_status advect_combine(cfd_blocks_s *B, const void *tmp6, const void *beta, i
   return CFD_OK;
 }
 
-cfd_status advect_accumulate(cfd_blocks_s *B, const void *field, const void *beta, void *out, int out_nops,
+cfd_status advect_accumulate(cfd_blocks_s *B, const void *fields, int nf, const void *beta, void *out, int out_nops,
                              int out_opidx, cfd_precision prec, int n_iter, void *work, size_t work_bytes,
                              cudaStream_t st) {
   int win;
-  cfd_status s = check_request(B, 1, prec, n_iter, &win);
+  cfd_status s = check_request(B, nf, prec, n_iter, &win);
   if (s != CFD_OK) return s;
-  if ((s = check_work(B, 1, prec, n_iter, work, work_bytes)) != CFD_OK) return s;
+  if ((s = check_work(B, nf, prec, n_iter, work, work_bytes)) != CFD_OK) return s;
   const int axes[3] = {2, 1, 0};
   if (prec != CFD_FP64_BANDED)
-    return dense_biased(B, field, 1, beta, axes, 3, 2, prec, n_iter, out, out_nops, out_opidx, true, work,
+    return dense_biased(B, fields, nf, beta, axes, 3, 2, prec, n_iter, out, out_nops, out_opidx, true, work,
                         work_bytes, st);
-  return run_biased(B, field, 1, beta, axes, 3, 2, n_iter, win, out, work, st, out_nops, out_opidx, true);
+  return run_biased(B, fields, nf, beta, axes, 3, 2, n_iter, win, out, work, st, out_nops, out_opidx, true);
 }
 
 }  // namespace cfd

@@ -171,12 +171,12 @@ enum KernelFamily { KF_EXCHANGE = 0, KF_LINE = 1, KF_RK = 2, KF_DENSE = 3, KF_HA
 void launch_begin(int family, cudaStream_t st);
 void launch_end(int family, cudaStream_t st);
 
-// biased.cu: out[slot out_opidx of out_nops per block] += sum_i beta^i_+ D_i[S+] f + beta^i_- D_i[S-] f
-// for one FP64 field (`work` as cfd_biased_workspace(B, 1, prec, n_iter))
-cfd_status advect_accumulate(cfd_blocks_s *B, const void *field, const void *beta, void *out, int out_nops,
+// biased.cu: out[block][field][slot out_opidx of out_nops] += sum_i beta^i_+ D_i[S-] f + beta^i_- D_i[S+] f
+// for nf fields (`work` as cfd_biased_workspace(B, nf, prec, n_iter))
+cfd_status advect_accumulate(cfd_blocks_s *B, const void *fields, int nf, const void *beta, void *out, int out_nops,
                              int out_opidx, cfd_precision prec, int n_iter, void *work, size_t work_bytes,
                              cudaStream_t st);
-// biased.cu: out slot = (accum_all ? out : 0) + sum_{i=x,y,z} beta^i (beta^i > 0 ? T[2i] : T[2i+1]),
+// biased.cu: out slot = (accum_all ? out : 0) + sum_{i=x,y,z} beta^i (beta^i > 0 ? T[2i+1] : T[2i]),
 // T = [block][field][6][N^3] (both biased derivatives of every axis)
 cfd_status advect_combine(cfd_blocks_s *B, const void *tmp6, const void *beta, int nf, void *out, int out_nops,
                           int out_opidx, bool accum_all, cudaStream_t st);

@@ -409,8 +409,8 @@ cfd_status lsrk_impl(const char *who, cfd_blocks_s *B, void *phi, void *K, const
     }
     if (beta) {
       // F_Phi (slot 1) += beta . grad Phi, F_K (slot 0) += beta . grad K, upwinded
-      if ((s = advect_accumulate(B, phi, beta, lap, 3, 1, prec, n_iter, bw, bws, st)) != CFD_OK) return s;
-      if ((s = advect_accumulate(B, K, beta, lap, 3, 0, prec, n_iter, bw, bws, st)) != CFD_OK) return s;
+      if ((s = advect_accumulate(B, phi, 1, beta, lap, 3, 1, prec, n_iter, bw, bws, st)) != CFD_OK) return s;
+      if ((s = advect_accumulate(B, K, 1, beta, lap, 3, 0, prec, n_iter, bw, bws, st)) != CFD_OK) return s;
     }
     for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
       const int N = B->sizes[gi];

@@ -183,6 +183,19 @@ def uniform_mesh(NM: int, N: int, g: int = 4, L: float = TWO_PI) -> Mesh:
     return Mesh(np.full(nb ** 3, N), origin, dx, neighbors, g, (nb, nb, nb))
 
 
+def periodic_box_mesh(nbx: int, nby: int, nbz: int, N: int, g: int = 4, L: float = TWO_PI) -> Mesh:
+    """Periodic box of nbx x nby x nbz blocks of N^3 with spacing L / (nbx N) on every axis (a
+    2D problem is a box one block thick in z); block index (bz*nby + by)*nbx + bx."""
+    idx = np.arange(nbx * nby * nbz)
+    bz, by, bx = idx // (nbx * nby), (idx // nbx) % nby, idx % nbx
+    origin = np.stack([bx * N, by * N, bz * N], 1)
+    neighbors = np.empty((len(idx), 26), np.int32)
+    for r, (dz, dy, dxx) in enumerate(DIRS):
+        neighbors[:, r] = (((bz + dz) % nbz) * nby + (by + dy) % nby) * nbx + (bx + dxx) % nbx
+    dx = np.full((len(idx), 3), L / (nbx * N))
+    return Mesh(np.full(len(idx), N), origin, dx, neighbors, g, (nbz, nby, nbx))
+
+
 def box_in_box_mesh(g: int = 4) -> Mesh:
     """448 blocks of 16^3 and 64 of 32^3 on [0, 2pi)^3.
 

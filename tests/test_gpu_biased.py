@@ -323,3 +323,37 @@ def test_shifted_wave_rejections(lib, torch):
         lib.cfd_shifted_wave_lsrk_step(Bk, t, t.clone(), tb, 0.01, T.lsrk2s_rk4_float(), 0.0, 4, 0, 0, work)
     assert e.value.status == lib.CFD_ERR_ARG
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec,n_iter", [(0, 0), (0, 1), (2, 1)])
+def test_advect_lsrk_parity(lib, torch, prec, n_iter):
+    """Two 2S steps of u_t = beta . grad u + KO for two fields with a mixed-sign shift vs the oracle."""
+    from oracle import timestep as T
+    NM, N, g, sigma, r, nf = 64, 16, 4, 0.04, 4, 2
+    fields = case_fields(31, nf)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    beta_g = [f(X, Y, Z) for f in shift_fields()]
+    _, _, _, bbuf = uniform_case(NM, N, g, shift_fields())
+    Bk = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    tu = torch.from_numpy(buf.copy()).cuda()
+    tb = torch.from_numpy(bbuf).cuda()
+    work = torch.empty(lib.cfd_advect_lsrk_workspace(Bk, nf, prec, n_iter), dtype=torch.uint8, device="cuda")
+    coef = T.lsrk2s_rk4_float()
+    dt = 0.3 * dx
+    b = biased_of("X2_d1")
+    us = [f(X, Y, Z) for f in fields]
+    for _ in range(2):
+        lib.cfd_advect_lsrk_step(Bk, tu, nf, tb, dt, coef, sigma, r, prec, n_iter, work)
+        us = [T.advect_lsrk_step(u, beta_g, dt, coef, b, (dx, dx, dx), N, g, n_iter, sigma, r) for u in us]
+    lib.cfd_sync_status(Bk)
+    E = N + 2 * g
+    nb = NM // N
+    I = slice(g, g + N)
+    got = tu.cpu().numpy().reshape(mesh.nblocks, nf, E, E, E)[:, :, I, I, I]
+    tol = 1e-12 if prec == 0 else 1e-7
+    for q in range(nf):
+        gq = C.blocks_to_global(got[:, q].reshape(nb, nb, nb, N, N, N))
+        assert rel_max(gq, us[q]) < tol, (q, rel_max(gq, us[q]))
+

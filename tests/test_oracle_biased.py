@@ -215,9 +215,27 @@ def test_upwind_choice_is_stable_and_the_opposite_is_not():
             assert lam.real.max() > 1e-3
 
 
+def test_shift_term_upwinding_is_stable_and_the_opposite_is_not():
+    """The right-hand-side term beta d_x u with the upwinding of advect_uniform (right-biased
+    where beta > 0, left-biased where beta < 0) has no growing mode for either sign of beta;
+    the opposite choice has eigenvalues with Re > 0."""
+    b = _biased("X2_d1")
+    n = 32
+    dx = 2 * np.pi / n
+    for beta in (0.7, -0.7):
+        good = -1 if beta > 0 else 1
+        for side, stable in ((good, True), (-good, False)):
+            A, Bm = B.cyclic_matrices(b, side, n, dx)
+            lam = np.linalg.eigvals(beta * np.linalg.solve(A, Bm))
+            if stable:
+                assert lam.real.max() < 1e-12
+            else:
+                assert lam.real.max() > 1e-3
+
+
 def test_advect_uniform_selects_the_upwind_side_pointwise():
-    """Eq. biasderapproxadv with a pointwise shift of both signs: where beta^x > 0 the
-    term equals beta^x times the left-biased derivative, where beta^x < 0 the right-biased
+    """Eq. biasderapproxadv with a pointwise shift of both signs (c = -beta): where beta^x > 0
+    the term equals beta^x times the right-biased derivative, where beta^x < 0 the left-biased
     one; beta^y = beta^z = 0.  Converged iteration = the global schemes."""
     b = _biased("Q1034_1_d1")
     NM, N, g = 32, 16, 4
@@ -233,7 +251,7 @@ def test_advect_uniform_selects_the_upwind_side_pointwise():
     got = C.blocks_to_global(B.advect_uniform(ext, beta, b, (dx, dx, dx), N, g, n_iter=4))
     dp = np.moveaxis(B.global_periodic(np.moveaxis(f, 2, 0), b, +1, dx), 0, 2)
     dm = np.moveaxis(B.global_periodic(np.moveaxis(f, 2, 0), b, -1, dx), 0, 2)
-    want = np.where(bx > 0, bx * dp, bx * dm)
+    want = np.where(bx > 0, bx * dm, bx * dp)
     assert rel_max(got, want) < 1e-12
     # the swapped choice is measurably different
-    assert rel_max(np.where(bx > 0, bx * dm, bx * dp), want) > 1e-6
+    assert rel_max(np.where(bx > 0, bx * dp, bx * dm), want) > 1e-6

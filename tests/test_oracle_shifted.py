@@ -20,9 +20,9 @@ def _biased(name):
 
 def test_shifted_wave_rhs_on_a_plane_wave():
     """Constant shift (beta^x > 0, beta^y < 0, beta^z = 0): with the iteration converged, a
-    mode Re(A e^{i k.x}) of (Phi, K) is mapped by the symbols: beta^x uses the left-biased
-    wavenumber, beta^y the right-biased one (Eq. biasderapproxadv), the Laplacian the
-    second-degree scheme's, the dissipation the Kreiss-Oliger symbol."""
+    mode Re(A e^{i k.x}) of (Phi, K) is mapped by the symbols: beta^x uses the right-biased
+    wavenumber, beta^y the left-biased one (Eq. biasderapproxadv with c = -beta), the
+    Laplacian the second-degree scheme's, the dissipation the Kreiss-Oliger symbol."""
     NM, N, g, r, sigma, n_iter = 32, 16, 4, 4, 0.04, 12
     dx = 2 * np.pi / NM
     x = (np.arange(NM) + 0.5) * dx
@@ -42,7 +42,7 @@ def test_shifted_wave_rhs_on_a_plane_wave():
     lam = 0.0
     q = 0.0
     for bi, ki in zip(bvec, k):
-        sch = X2 if bi > 0 else B.mirror(X2)
+        sch = B.mirror(X2) if bi > 0 else X2
         S += bi * 1j * SC.modified_wavenumber(sch, ki * dx) / dx
         lam += -SC.modified_wavenumber(q2, ki * dx).real / dx ** 2
         q += T.ko_symbol(r, sigma, dx, ki)
@@ -51,7 +51,7 @@ def test_shifted_wave_rhs_on_a_plane_wave():
     assert np.max(np.abs(fp - want_p)) < 1e-10 * np.max(np.abs(want_p))
     assert np.max(np.abs(fk - want_k)) < 1e-10 * np.max(np.abs(want_k))
     # taking the other bias on either axis changes the result well above that tolerance
-    S_bad = bvec[0] * 1j * SC.modified_wavenumber(B.mirror(X2), k[0] * dx) / dx + \
+    S_bad = bvec[0] * 1j * SC.modified_wavenumber(X2, k[0] * dx) / dx + \
         bvec[1] * 1j * SC.modified_wavenumber(B.mirror(X2), k[1] * dx) / dx
     bad = ((Ap * S_bad + Ak + q * Ap) * np.exp(1j * th)).real
     assert np.max(np.abs(bad - want_p)) > 1e-8 * np.max(np.abs(want_p))
@@ -112,3 +112,40 @@ def test_exponential_integration_reproduces_the_pade_error_ratio():
     q3 = _ei_error(oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2"))
     assert abs(e3 / p2 - 11.2) < 0.1
     assert p2 / q3 > 5
+
+
+def test_advection_step_advances_a_mode_by_the_stability_polynomial():
+    """u_t = beta . grad u + KO with a constant shift (beta^x > 0, beta^y < 0): with the iteration
+    converged a mode Re(A e^{i k.x}) is multiplied by R(dt (S + q)) per 2S step, S the upwinded
+    symbol sum_i beta_i i eta~_i / dx (right-biased wavenumber where beta_i > 0, left-biased
+    where beta_i < 0), q the Kreiss-Oliger symbol and R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24;
+    |R| <= 1 for this mode (no growth)."""
+    NM, N, g, r, sigma, n_iter = 32, 16, 4, 4, 0.04, 10
+    dx = 2 * np.pi / NM
+    x = (np.arange(NM) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    k = (4, -3, 2)
+    th = k[0] * X + k[1] * Y + k[2] * Z
+    A = 0.7 - 0.4j
+    u = (A * np.exp(1j * th)).real
+    bvec = (0.5, -0.3, 0.0)
+    beta = [np.full_like(X, v) for v in bvec]
+    b = _biased("Q1034_1_d1")
+    q34, _ = B.tuned_Q1034(1)
+    dt = 0.3 * dx
+    u1 = T.advect_lsrk_step(u, beta, dt, T.lsrk2s_rk4_float(), b, (dx, dx, dx), N, g, n_iter, sigma, r)
+    S = 0j
+    q = 0.0
+    for bi, ki in zip(bvec, k):
+        sch = B.mirror(q34) if bi > 0 else q34
+        S += bi * 1j * SC.modified_wavenumber(sch, ki * dx) / dx
+        q += T.ko_symbol(r, sigma, dx, ki)
+    z = dt * (S + q)
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    want = (R * A * np.exp(1j * th)).real
+    assert np.max(np.abs(u1 - want)) < 1e-11 * np.max(np.abs(want))
+    assert abs(R) <= 1.0
+    # the step moves the mode: without the shift it is only damped by the dissipation
+    u0 = T.advect_lsrk_step(u, [0 * X] * 3, dt, T.lsrk2s_rk4_float(), b, (dx, dx, dx), N, g, n_iter, sigma, r)
+    assert np.max(np.abs(u0 - u1)) > 1e-2 * np.max(np.abs(u))
+
