@@ -508,11 +508,12 @@ cfd_status check_work(cfd_blocks_s *B, int nf, cfd_precision prec, int n_iter, v
 
 // Upwind blend of the two biased derivatives of every axis (tensor-core path): one thread per
 // interior point of one (block, field); axes added in the order x, y, z.
-template <typename T>
-__global__ void k_advect_combine(const T *__restrict__ tmp, const T *__restrict__ beta, T *out,
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_advect_combine(const T *__restrict__ tmp, const T *__restrict__ beta, T *out,
                                  const int *__restrict__ blocks, const long long *__restrict__ extpre,
-                                 const long long *__restrict__ intpre, int N, int g, int nf, int out_nops,
+                                 const long long *__restrict__ intpre, int N_, int g, int nf, int out_nops,
                                  int out_opidx, int accum_all) {
+  const int N = NC ? NC : N_;
   const int n3 = N * N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
@@ -525,15 +526,17 @@ __global__ void k_advect_combine(const T *__restrict__ tmp, const T *__restrict_
   const T *bt = beta + 3 * extpre[b] + ((long long)(z + g) * E + (y + g)) * E + (x + g);
   const T *tp = tmp + (long long)nf * 6 * intpre[b] + (long long)q * 6 * n3 + i;
   T *o = out + (long long)nf * out_nops * intpre[b] + ((long long)q * out_nops + out_opidx) * n3 + i;
+  // all loads issued before any use: the three shift components, then one derivative per axis
+  // (beta > 0: the right-biased one, slot 2c+1; beta < 0: the left-biased one, slot 2c)
+  T bv[3], dv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) bv[c] = __ldg(bt + c * E3);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dv[c] = __ldg(tp + (2 * c + (sign_bits(bv[c]) == 1 ? 1 : 0)) * (long long)n3);
   double acc = accum_all ? static_cast<double>(*o) : 0.0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const T braw = __ldg(bt + c * E3);
-    const int sg = sign_bits(braw);
-    const double bb = static_cast<double>(braw);
-    // beta > 0: the right-biased derivative (slot 2c+1); beta < 0: the left-biased one (slot 2c)
-    const double t = sg == 1 ? bb * static_cast<double>(__ldg(tp + (2 * c + 1) * n3))
-                             : (sg == 2 ? bb * static_cast<double>(__ldg(tp + (2 * c) * n3)) : 0.0);
+    const double t = sign_bits(bv[c]) == 0 ? 0.0 : static_cast<double>(bv[c]) * static_cast<double>(dv[c]);
     acc = (c == 0 && !accum_all) ? t : acc + t;
   }
   *o = static_cast<T>(acc);
@@ -548,15 +551,19 @@ cfd_status advect_combine(cfd_blocks_s *B, const void *tmp6, const void *beta, i
     const int n3 = N * N * N;
     dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)(B->groups[gi].size() * nf));
     launch_begin(KF_BIASED, st);
-    if (B->dtype == CFD_F32)
-      k_advect_combine<float><<<grid, 256, 0, st>>>(static_cast<const float *>(tmp6), static_cast<const float *>(beta),
-                                                   static_cast<float *>(out), B->d_groups[gi], B->d_extpre,
-                                                   B->d_intpre, N, B->ng, nf, out_nops, out_opidx, accum_all);
-    else
-      k_advect_combine<double><<<grid, 256, 0, st>>>(static_cast<const double *>(tmp6),
-                                                     static_cast<const double *>(beta), static_cast<double *>(out),
-                                                     B->d_groups[gi], B->d_extpre, B->d_intpre, N, B->ng, nf,
-                                                     out_nops, out_opidx, accum_all);
+    auto go = [&](auto tag, auto nc) {
+      using T = decltype(tag);
+      k_advect_combine<T, decltype(nc)::value><<<grid, 256, 0, st>>>(
+          static_cast<const T *>(tmp6), static_cast<const T *>(beta), static_cast<T *>(out), B->d_groups[gi],
+          B->d_extpre, B->d_intpre, N, B->ng, nf, out_nops, out_opidx, accum_all);
+    };
+    auto by_n = [&](auto tag) {
+      if (N == 32) go(tag, std::integral_constant<int, 32>());
+      else if (N == 16) go(tag, std::integral_constant<int, 16>());
+      else go(tag, std::integral_constant<int, 0>());
+    };
+    if (B->dtype == CFD_F32) by_n(float());
+    else by_n(double());
     launch_end(KF_BIASED, st);
     cfd_status s = cuda_fail(cudaGetLastError(), "k_advect_combine launch");
     if (s != CFD_OK) return s;
