@@ -22,10 +22,12 @@ struct KoArgs {
   int c[13];               // (D_+)^r (D_-)^r stencil, m = -r..r
 };
 
-// F = sum_i Q_i[u] (0 without dissipation), axes x, y, z, taps m = -r..r in FP64.
-template <int NC>
+// F = sum_i Q_i[u] (0 without dissipation), axes x, y, z, taps m = -r..r in FP64.  RC: the
+// stencil order r as a compile-time constant (0: taken from A.r).
+template <int NC, int RC>
 __global__ void k_ko_fields(const KoArgs A) {
   const int N = NC ? NC : A.N, g = A.g, E = N + 2 * g;
+  const int r = RC ? RC : A.r;
   const int n3 = N * N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
@@ -37,11 +39,13 @@ __global__ void k_ko_fields(const KoArgs A) {
   const long long e = (long long)A.nf * A.extpre[b] + q * E3 + ((long long)(z + g) * E + (y + g)) * E + (x + g);
   double f = 0.0;
   if (A.ko_on) {
-    const long long stride[3] = {1, E, (long long)E * E};   // x, y, z
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
+      const long long st = a == 0 ? 1ll : (a == 1 ? (long long)E : (long long)E * E);   // x, y, z
       const double w = A.ko * A.scale[(b * 2 + 0) * 3 + a];
       double s = 0.0;
-      for (int m = -A.r; m <= A.r; ++m) s = fma((double)A.c[m + A.r], A.u[e + m * stride[a]], s);
+#pragma unroll
+      for (int m = -r; m <= r; ++m) s = fma((double)A.c[m + r], __ldg(A.u + e + m * st), s);
       f = fma(w, s, f);
     }
   }
@@ -160,9 +164,10 @@ extern "C" cfd_status cfd_advect_lsrk_step(cfd_blocks_t B, void *u, int nfields,
       A.blocks = B->d_groups[gi];
       A.N = N;
       launch_begin(KF_RK, st);
-      if (N == 32) k_ko_fields<32><<<grid, 256, 0, st>>>(A);
-      else if (N == 16) k_ko_fields<16><<<grid, 256, 0, st>>>(A);
-      else k_ko_fields<0><<<grid, 256, 0, st>>>(A);
+      const bool r4 = K.ko_on && K.r == 4;
+      if (N == 32) { if (r4) k_ko_fields<32, 4><<<grid, 256, 0, st>>>(A); else k_ko_fields<32, 0><<<grid, 256, 0, st>>>(A); }
+      else if (N == 16) { if (r4) k_ko_fields<16, 4><<<grid, 256, 0, st>>>(A); else k_ko_fields<16, 0><<<grid, 256, 0, st>>>(A); }
+      else k_ko_fields<0, 0><<<grid, 256, 0, st>>>(A);
       launch_end(KF_RK, st);
       if ((s = cuda_fail(cudaGetLastError(), "k_ko_fields launch")) != CFD_OK) return s;
     }

@@ -357,3 +357,47 @@ def test_advect_lsrk_parity(lib, torch, prec, n_iter):
         gq = C.blocks_to_global(got[:, q].reshape(nb, nb, nb, N, N, N))
         assert rel_max(gq, us[q]) < tol, (q, rel_max(gq, us[q]))
 
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_biased_uneven_blocks_analytic_ghosts(lib, torch, side):
+    """Blocks of 8^3 and 16^3 whose ghosts at the size interface are sampled from the analytic
+    field (neighbour -1): closed biased systems per block; the tensor cores refuse the 8^3 group."""
+    from paper_2302_14858_gb300 import workloads as W
+    from tests.test_gpu_banded import mini_box_in_box
+    mesh = mini_box_in_box()
+    g = mesh.g
+    fields = W.workload_fields(4)[:2]
+    per_block = W.sample(mesh, fields)
+    buf = W.pack(per_block)
+    Bk = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    mask = lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ
+    out = run_biased(lib, torch, Bk, buf, 2, mask, side, 0)
+    got = W.unpack(out, mesh, 2, interior=True, nops=3)
+    b_ = biased_of("X2_d1")
+    worst = 0.0
+    for q in range(2):
+        for i, c in enumerate(AXES):
+            want = [B.biased_uniform(per_block[b][q][None, None, None], b_, side, mesh.dx[b], int(mesh.n[b]), g,
+                                     (c,), 0)[c][0, 0, 0] for b in range(mesh.nblocks)]
+            wmax = max(np.abs(w).max() for w in want)
+            worst = max(worst, max(np.abs(got[b][q, i] - want[b]).max() for b in range(mesh.nblocks)) / wmax)
+    assert worst < TOL64
+    with pytest.raises(lib.CfdError) as e:
+        run_biased(lib, torch, Bk, buf, 2, mask, side, 0, prec=2)
+    assert e.value.status == lib.CFD_ERR_UNSUPPORTED
+
+
+def test_biased_float32_tensor_cores(lib, torch):
+    """FP32 fields through the dense biased operators (exact slices, FP32 outputs)."""
+    NM, N, g = 64, 16, 4
+    fields = case_fields(13, 1)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    buf32 = buf.astype(np.float32)
+    blocks = bind(lib, "Q1034_1_d1", mesh, g, lib.CFD_F32)
+    got = run_biased(lib, torch, blocks, buf32, 1, lib.CFD_OP_DY, 1, 1, np.float32, prec=2)
+    got = got.reshape(mesh.nblocks, N, N, N).astype(np.float64)
+    E = N + 2 * g
+    ext = buf32.reshape(mesh.nblocks, E, E, E).astype(np.float64).reshape(exts[0].shape)
+    want = B.biased_uniform(ext, biased_of("Q1034_1_d1"), 1, (dx, dx, dx), N, g, ("y",), 1)["y"]
+    assert rel_max(got, want.reshape(mesh.nblocks, N, N, N)) < 2e-6
