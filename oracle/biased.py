@@ -31,6 +31,9 @@ Scheme design (exact rationals, ``oracle.schemes`` machinery)
   embedded f^{(2)} approximated by (2)E_{M+2}:  lam U_M^- + (1 - lam) V_{M+1}^-,
   and its closure X-bar_M^- = the xi closure of X_M^- with n = 2M+4
   (Tab. ccux_deg_one_col; lam is the tabulated sigma).
+* ``ccu_lambda(M, lam_max)`` the weight selection rule of Sec. domdec_drp (lam_max = 1, or 2
+  for M = 3 where the combination overestimates eta at lam <= 1); reading: lam is lowered in
+  steps of 1/100 (the printed precision) while Re eta~ <= eta holds on (0, pi].
 
 Block systems (FP64, numpy)
 ---------------------------
@@ -198,6 +201,31 @@ def ccu_x(M: int, lam) -> Tuple[SC.Scheme, object, SC.Scheme]:
     X = combine(lam, U, ucd_fast(M + 1))
     xi, Xb = xi_closure(X, 2 * M + 4)
     return X, xi, Xb
+
+
+def ccu_x_interior(M: int, lam) -> SC.Scheme:
+    """X_M^- without its closure: lam U_M^- (f'' from (2)E_{M+2}) + (1 - lam) V_{M+1}^-."""
+    return combine(lam, embed_second(ucd_slow(M), M + 2), ucd_fast(M + 1))
+
+
+def ccu_lambda(M: int, lam_max, step=Fraction(1, 100), n_eta: int = 2000):
+    """The weight of Eq. LCslowfast by the selection rule of Sec. domdec_drp: start at lam_max and
+    reduce lam (in steps of ``step``) while Re eta~ <= eta holds on (0, pi]; return the last lam
+    for which it holds (None if lam_max already fails).  The comparison is on ``n_eta`` points
+    with a 1e-12 tolerance."""
+    import numpy as np
+    etas = np.linspace(1e-3, np.pi, n_eta)
+
+    def ok(lam):
+        X = ccu_x_interior(M, lam)
+        return max(SC.modified_wavenumber(X, e).real - e for e in etas) <= 1e-12
+
+    lam = Fraction(lam_max)
+    if not ok(lam):
+        return None
+    while lam - step >= 0 and ok(lam - step):
+        lam -= step
+    return lam
 
 
 def tuned_Q1034(eta_c=1) -> Tuple[SC.Scheme, SC.Scheme]:

@@ -91,6 +91,14 @@ def test_ccu_x_reproduces_table(M):
     assert e[2 * M + 2] == eb[2 * M + 2] and e[2 * M + 3] == eb[2 * M + 3]
 
 
+@pytest.mark.parametrize("M,lam_max,printed", [(1, 1, "37/100"), (2, 1, "86/100"), (3, 2, "146/100")])
+def test_ccu_weight_selection_rule_gives_the_printed_sigma(M, lam_max, printed):
+    """Sec. domdec_drp: start at lam_max (1; 2 for M = 3) and lower lam until Re eta~ <= eta on
+    (0, pi] would fail; the last admissible lam (1/100 steps) is the sigma of
+    Tab. ccux_deg_one_col, and lam - 1/100 overestimates eta somewhere."""
+    assert B.ccu_lambda(M, lam_max) == Fraction(printed)
+
+
 @pytest.mark.parametrize("maker", ["U2", "V3", "X2"])
 def test_mirror_conjugates_eps(maker):
     """eps[S^+] = eps[S^-]^* (captions of Tabs. ucd_slow, ucd_fast, ccux_deg_one_col)."""
