@@ -74,7 +74,14 @@ DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 # dram__bytes_write.sum).  The 256^3 workload exceeds the capture-size rule, so the same kernel
 # was captured on 128^3 with the same 32^3 blocks (one step = 6 launches, 1051.2 MB) and scaled
 # by the 8x points: 8409.6 MB per step / 6 launches.  profiles/k_dense_tc_exact_cfd128_b32_f4.md
-MEASURED_TRAFFIC = {("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1401.6e6}
+MEASURED_TRAFFIC = {("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1401.6e6,
+                    # upwinded advection, n_iter = 1: captured on 128^3 with the same 32^3 blocks
+                    # (profiles/k_dense_biased_advect128_b32_x2_f4.md: halo pass 86.8 MB, final pass
+                    # 173.3 MB) and scaled by the 8x points; mean over the 3 halo + 3 final launches
+                    ("advect256_b32_x2_f4_fp64", "tc_bf16_exact", 1): 1040.4e6,
+                    # the FP64 k_biased launches of the same step (profiles/k_biased_fp64_advect128_b32_x2_f4.md:
+                    # final pass 137.6 MB, halo pass 108.5 MB at 128^3), scaled the same way
+                    ("advect256_b32_x2_f4_fp64", "fp64_banded", 1): 984.4e6}
 
 
 def scheme_descs():
@@ -804,7 +811,9 @@ def run_advect(args, spec):
         roof = {"kernel": "k_dense (tcgen05 BF16 digit-slice GEMM, biased operators D+ and D-)", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_point_field": round(per_pf, 2), "traffic": None,
+                "algorithmic_bytes_per_point_field": round(per_pf, 2),
+                "traffic": MEASURED_TRAFFIC.get((args.workload, args.prec, n_iter)),
+                "algorithmic_bytes_per_launch": round(per_pf * units / max(ndl / prof_steps, 1)),
                 "launches_per_step": ndl / prof_steps, "avg_launch_ms": round(tdl / max(ndl, 1), 5),
                 "share_of_step": round(tdl / (ms_prof * prof_steps), 4),
                 "blend": {"kernel": "k_advect_combine", "launches_per_step": nl / prof_steps,
@@ -823,7 +832,8 @@ def run_advect(args, spec):
                 "mixed_sign_pencils_xyz": [round(v, 4) for v in mixed],
                 "hbm_achieved_gbs": round(byts / (tl * 1e-3) / 1e9, 1), "hbm_peak_gbs": hbm,
                 "algorithmic_bytes_per_point_field": round(16 + 24 / nf, 2),
-                "traffic": None, "launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
+                "traffic": MEASURED_TRAFFIC.get((args.workload, args.prec, n_iter)),
+                "launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
                 "share_of_step": round(tl / (ms_prof * prof_steps), 4),
                 "events_region": {"steps": prof_steps, "ms_per_step": round(ms_prof, 5)}}
 
