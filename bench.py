@@ -80,8 +80,8 @@ MEASURED_TRAFFIC = {("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1401.6e6,
                     # 173.3 MB) and scaled by the 8x points; mean over the 3 halo + 3 final launches
                     ("advect256_b32_x2_f4_fp64", "tc_bf16_exact", 1): 1040.4e6,
                     # the FP64 k_biased launches of the same step (profiles/k_biased_fp64_advect128_b32_x2_f4.md:
-                    # final pass 137.6 MB, halo pass 108.5 MB at 128^3), scaled the same way
-                    ("advect256_b32_x2_f4_fp64", "fp64_banded", 1): 984.4e6}
+                    # final pass 138.0 MB, halo pass 108.3 MB at 128^3), scaled the same way
+                    ("advect256_b32_x2_f4_fp64", "fp64_banded", 1): 985.2e6}
 
 
 def scheme_descs():
