@@ -467,6 +467,23 @@ def max_abs_diff_per_field_op(out, ref, mesh, nf, nops, torch):
     return errs, maxs
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """The job's time is the slowest rank's: all-reduce MAX over the process group (identity on
+    a single process).  ``device`` is the CUDA device for NCCL, None for a CPU (gloo) group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput in G units/s: every rank processes units_per_rank in ms (the max)."""
+    return units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def timed(step, steps, stream, torch):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -573,12 +590,8 @@ def main():
     ms_prof = timed(step, prof_steps, stream, torch)
     prof = {name: cfd.cfd_profile_read(fid) for name, fid in cfd.KERNEL_FAMILIES.items()}
     cfd.cfd_profile_enable(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = units * world / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ms_step, dev)
+    value = whole_job_value(units, world, ms_step)
     ms_total = ms_prof * prof_steps
 
     # roofline of the dominant kernel family, from the per-launch event times of the timed region
@@ -776,11 +789,8 @@ def run_advect(args, spec):
     ms_prof = timed(step, prof_steps, stream, torch)
     prof = {name: cfd.cfd_profile_read(fid) for name, fid in cfd.KERNEL_FAMILIES.items()}
     cfd.cfd_profile_enable(False)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = units * world / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ms_step, dev)
+    value = whole_job_value(units, world, ms_step)
 
     nl, tl = prof["biased"]
     fpp = advect_flops_per_point_axis(9, n_iter, N, g) * 3
@@ -977,11 +987,7 @@ def run_adv2d(args, spec):
     ms, err = run(prec, args.steps)
     clk = clocks.stop()
     launches = cfd.cfd_kernel_launches() - launches0
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev)
     units = NM * NM * N * 4
     compare = None
     if not args.no_compare and prec != PREC["fp64_banded"]:
@@ -992,7 +998,7 @@ def run_adv2d(args, spec):
     if rank == 0:
         line = {
             "metric": ADV2D_METRIC, "value":
-                round(units * world / (ms * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s", "n_gpus": world,
+                round(whole_job_value(units, world, ms), 4), "unit": "Gpoint-ops/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (the paper's analytic profile g(x) h(y))",
@@ -1121,11 +1127,7 @@ def run_wave(args, spec):
     ms, err = run(prec, args.steps, True)
     clk = clocks.stop()
     launches = cfd.cfd_kernel_launches() - launches0
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev)
     # 3 second-derivative ops per point and stage (+ the two upwinded advective terms when shifted)
     units = (3 + (2 if shift is not None else 0)) * NM ** 3 * 4
     cpu = cpu_baseline(spec) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
@@ -1137,7 +1139,7 @@ def run_wave(args, spec):
                    "speedup_vs_fp64_banded": round(ms64 / ms, 3)}
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(units * world / (ms * 1e-3) / 1e9, 4), "unit": "Gpoint-ops/s",
+            "metric": METRIC, "value": round(whole_job_value(units, world, ms), 4), "unit": "Gpoint-ops/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded plane waves)",
