@@ -385,6 +385,34 @@ cfd_status cfd_advect_lsrk_step(cfd_blocks_t blocks, void *u, int nfields, const
                                 const cfd_lsrk_desc *rk, double sigma, int ko_r, cfd_precision prec, int n_iter,
                                 void *work, size_t work_bytes, void *stream);
 
+/*
+ * Ghost regions between processes.  When the MeshBlocks of one problem are
+ * split over several processes (one GPU each), a process binds its own
+ * blocks with -1 for the directions whose neighbour lives elsewhere, fills
+ * the local ghosts with cfd_exchange_ghosts, and moves the remote ones with
+ * these plans (the remote part of matrix G, Eq. example_G); the transport
+ * between processes (e.g. NCCL send/recv of the buffers) is the caller's.
+ *   items  host [n][2] = (local block, direction r, numbered as CFD_NDIRS).
+ *          In a pack plan the block is the one that owns the data and r is
+ *          the direction of the ghost region as seen from the receiving
+ *          neighbour: pack copies the owner's interior slab that fills that
+ *          region (ghost cell c of the receiver takes the owner's value at
+ *          c - d N, d the unit offset of r).  In an unpack plan the block is
+ *          the receiver and r its ghost region.
+ *  Buffer: the items in order; per item nfields slabs of the region's shape
+ *  (g or N per axis), (z, y, x) order, field dtype.  A pack plan on the owner
+ *  and an unpack plan on the receiver that list the same regions in the same
+ *  order move exactly the values cfd_exchange_ghosts would copy.
+ * The plan keeps a device copy of the items (freed by cfd_halo_plan_destroy).
+ */
+typedef struct cfd_halo_plan_s *cfd_halo_plan_t;
+cfd_status cfd_halo_plan_create(cfd_blocks_t blocks, const int *items, int n, cfd_halo_plan_t *out);
+/* Buffer bytes for `nfields` fields. */
+cfd_status cfd_halo_plan_bytes(cfd_halo_plan_t plan, int nfields, size_t *bytes);
+cfd_status cfd_halo_pack(cfd_halo_plan_t plan, const void *fields, int nfields, void *buf, void *stream);
+cfd_status cfd_halo_unpack(cfd_halo_plan_t plan, void *fields, int nfields, const void *buf, void *stream);
+void cfd_halo_plan_destroy(cfd_halo_plan_t plan);
+
 /* Wait for `stream`, then read and clear the device status word of the
  * handle: CFD_OK, CFD_ERR_TIMEOUT or CFD_ERR_DEVICE_ASSERT. */
 cfd_status cfd_sync_status(cfd_blocks_t blocks, void *stream);

@@ -45,7 +45,8 @@ EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd
            "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static",
            "cfd_scheme_set_biased", "cfd_biased_workspace", "cfd_apply_biased", "cfd_advect",
            "cfd_shifted_wave_workspace", "cfd_shifted_wave_lsrk_step", "cfd_advect_lsrk_workspace",
-           "cfd_advect_lsrk_step")
+           "cfd_advect_lsrk_step", "cfd_halo_plan_create", "cfd_halo_plan_bytes", "cfd_halo_pack",
+           "cfd_halo_unpack", "cfd_halo_plan_destroy")
 KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense_halo": 4, "biased": 5}
 
 
@@ -123,6 +124,16 @@ _lib.cfd_advect_lsrk_workspace.restype = c_int
 _lib.cfd_advect_lsrk_step.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_double, POINTER(LsrkDesc), c_double,
                                       c_int, c_int, c_int, c_void_p, c_size_t, c_void_p]
 _lib.cfd_advect_lsrk_step.restype = c_int
+_lib.cfd_halo_plan_create.argtypes = [c_void_p, POINTER(c_int), c_int, POINTER(c_void_p)]
+_lib.cfd_halo_plan_create.restype = c_int
+_lib.cfd_halo_plan_bytes.argtypes = [c_void_p, c_int, POINTER(c_size_t)]
+_lib.cfd_halo_plan_bytes.restype = c_int
+_lib.cfd_halo_pack.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p]
+_lib.cfd_halo_pack.restype = c_int
+_lib.cfd_halo_unpack.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p]
+_lib.cfd_halo_unpack.restype = c_int
+_lib.cfd_halo_plan_destroy.argtypes = [c_void_p]
+_lib.cfd_halo_plan_destroy.restype = None
 _lib.cfd_sync_status.argtypes = [c_void_p, c_void_p]
 _lib.cfd_sync_status.restype = c_int
 _lib.cfd_kernel_launches.argtypes = []
@@ -362,6 +373,43 @@ def cfd_advect_lsrk_step(blocks: Blocks, u, nfields: int, beta, dt: float, coef,
     _check(_lib.cfd_advect_lsrk_step(blocks.handle, _ptr(u), nfields, _ptr(beta), float(dt), ctypes.byref(desc),
                                      float(sigma), int(ko_r), prec, n_iter, _ptr(work), _nbytes(work),
                                      _stream(stream)))
+
+
+class HaloPlan:
+    """Owning wrapper of cfd_halo_plan_t (keeps its Blocks alive)."""
+
+    def __init__(self, handle: int, blocks: Blocks, n: int):
+        self.handle = handle
+        self.blocks = blocks
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.cfd_halo_plan_destroy(self.handle)
+            self.handle = None
+
+
+def cfd_halo_plan_create(blocks: Blocks, items) -> HaloPlan:
+    """items: sequence of (local block, direction) pairs (see include/cfd.h)."""
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(items, dtype=np.int32).reshape(-1, 2))
+    h = c_void_p()
+    _check(_lib.cfd_halo_plan_create(blocks.handle, arr.ctypes.data_as(POINTER(c_int)), len(arr), ctypes.byref(h)))
+    return HaloPlan(h.value, blocks, len(arr))
+
+
+def cfd_halo_plan_bytes(plan: HaloPlan, nfields: int) -> int:
+    n = c_size_t()
+    _check(_lib.cfd_halo_plan_bytes(plan.handle, nfields, ctypes.byref(n)))
+    return n.value
+
+
+def cfd_halo_pack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
+    _check(_lib.cfd_halo_pack(plan.handle, _ptr(fields), nfields, _ptr(buf), _stream(stream)))
+
+
+def cfd_halo_unpack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
+    _check(_lib.cfd_halo_unpack(plan.handle, _ptr(fields), nfields, _ptr(buf), _stream(stream)))
 
 
 def cfd_sync_status(blocks: Blocks, stream=None):
