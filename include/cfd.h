@@ -6,6 +6,10 @@
  * split into MeshBlocks with ghost layers.  Each block solves its own banded
  * system closed by explicit, error-matched closures (Eq. sch_cent_om), with
  * optional hybrid matching-communication iterations (Eq. iter_center_P).
+ * It also applies biased (upwind) first-degree schemes with their
+ * single-point closures (Eqs. defChenSchemes, closure_left_X, iter_left_X),
+ * the upwinded shift-advection term built from them (Eq. biasderapproxadv),
+ * and time steps of the wave, shifted-wave and advection systems.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
