@@ -401,3 +401,79 @@ def test_biased_float32_tensor_cores(lib, torch):
     ext = buf32.reshape(mesh.nblocks, E, E, E).astype(np.float64).reshape(exts[0].shape)
     want = B.biased_uniform(ext, biased_of("Q1034_1_d1"), 1, (dx, dx, dx), N, g, ("y",), 1)["y"]
     assert rel_max(got, want.reshape(mesh.nblocks, N, N, N)) < 2e-6
+
+
+@pytest.mark.parametrize("name,g", [("X1_d1", 4), ("X3_d1", 6)])
+@pytest.mark.parametrize("side", [1, -1])
+def test_biased_tensor_cores_other_widths(lib, torch, name, g, side):
+    """X_1 (interior -3..3) and X_3 (-5..5, closure to 6, ng = 6: K = N + 2g + 4 = 48 for 32^3)
+    through the dense biased operators with one iteration."""
+    check_biased(lib, torch, name, 64, 32 if name == "X3_d1" else 16, g, side, 1, nf=1, prec=2)
+
+
+def mini_two_sizes(g=4):
+    """4^3 coarse blocks of 16^3 on [0, 2pi)^3 minus the octant [0, pi)^3, which holds 2^3 fine
+    blocks of 32^3 at half the spacing; ghosts facing the other size are the caller's (-1)."""
+    from paper_2302_14858_gb300 import workloads as W
+    nc = 4
+    ns, origins, ds = [], [], []
+    ci, fi = {}, {}
+    for bz in range(nc):
+        for by in range(nc):
+            for bx in range(nc):
+                if bx < 2 and by < 2 and bz < 2:
+                    continue
+                ci[(bz, by, bx)] = len(ns)
+                ns.append(16)
+                origins.append((bx * 16, by * 16, bz * 16))
+                ds.append(2 * np.pi / 64)
+    for bz in range(2):
+        for by in range(2):
+            for bx in range(2):
+                fi[(bz, by, bx)] = len(ns)
+                ns.append(32)
+                origins.append((bx * 32, by * 32, bz * 32))
+                ds.append(np.pi / 64)
+    nbr = np.full((len(ns), 26), -1, np.int32)
+    for (bz, by, bx), b in ci.items():
+        for r, (dz, dy, dxx) in enumerate(W.DIRS):
+            nbr[b, r] = ci.get(((bz + dz) % nc, (by + dy) % nc, (bx + dxx) % nc), -1)
+    for (bz, by, bx), b in fi.items():
+        for r, (dz, dy, dxx) in enumerate(W.DIRS):
+            nbr[b, r] = fi.get((bz + dz, by + dy, bx + dxx), -1)
+    dx = np.repeat(np.asarray(ds)[:, None], 3, 1)
+    return W.Mesh(np.asarray(ns), np.asarray(origins), dx, nbr, g)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_advect_two_block_sizes_analytic_ghosts(lib, torch, prec):
+    """Upwinded advection on blocks of 16^3 and 32^3 (analytic ghosts at the size interface,
+    closures only) on both arithmetics, against the oracle block by block."""
+    from paper_2302_14858_gb300 import workloads as W
+    mesh = mini_two_sizes()
+    g = mesh.g
+    fields = W.workload_fields(4)[:2]
+    per_block = W.sample(mesh, fields)
+    beta_blocks = W.sample(mesh, shift_fields())
+    buf, bbuf = W.pack(per_block), W.pack(beta_blocks)
+    Bk = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    dev = torch.device("cuda", 0)
+    nint = sum(int(n) ** 3 for n in mesh.n)
+    out = torch.zeros(nint * 2, dtype=torch.float64, device=dev)
+    work = torch.empty(max(lib.cfd_biased_workspace(Bk, 2, prec, 0), 256), dtype=torch.uint8, device=dev)
+    lib.cfd_advect(Bk, torch.from_numpy(buf).to(dev), 2, torch.from_numpy(bbuf).to(dev), prec, 0, out, work)
+    lib.cfd_sync_status(Bk)
+    got = W.unpack(out.cpu().numpy(), mesh, 2, interior=True, nops=1)
+    b_ = biased_of("X2_d1")
+    worst = 0.0
+    for q in range(2):
+        want, gotq = [], []
+        for b in range(mesh.nblocks):
+            N = int(mesh.n[b])
+            I = slice(g, g + N)
+            beta = [beta_blocks[b][c][I, I, I][None, None, None] for c in range(3)]
+            want.append(B.advect_uniform(per_block[b][q][None, None, None], beta, b_, mesh.dx[b], N, g, 0)[0, 0, 0])
+            gotq.append(got[b][q, 0])
+        wmax = max(np.abs(w).max() for w in want)
+        worst = max(worst, max(np.abs(a - w).max() for a, w in zip(gotq, want)) / wmax)
+    assert worst < (TOL64 if prec == 0 else TOL_TC), worst
