@@ -477,3 +477,32 @@ def test_advect_two_block_sizes_analytic_ghosts(lib, torch, prec):
         wmax = max(np.abs(w).max() for w in want)
         worst = max(worst, max(np.abs(a - w).max() for a, w in zip(gotq, want)) / wmax)
     assert worst < (TOL64 if prec == 0 else TOL_TC), worst
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_biased_slab_mixed_cyclic_and_decomposed_axes(lib, torch, prec):
+    """A slab of 4 x 4 x 1 blocks of 16^3: x and y decomposed (one iteration), z one block thick
+    and therefore cyclic (the undecomposed periodic scheme) -- on both arithmetics."""
+    from paper_2302_14858_gb300 import workloads as W
+    N, g = 16, 4
+    mesh = W.periodic_box_mesh(4, 4, 1, N, g)
+    dx = 2 * np.pi / 64
+    x = (np.arange(64) + 0.5) * dx
+    z = (np.arange(16) + 0.5) * dx
+    Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+    fg = np.sin(3 * X - Y) * np.cos(2 * Y) + 0.3 * np.sin(X + 5 * 2 * np.pi * Z / (16 * dx))
+    ext = C.ghost_fill_3d(fg, N, g)                   # (1, 4, 4, E, E, E)
+    E = N + 2 * g
+    buf = ext.reshape(mesh.nblocks, E, E, E).reshape(-1)
+    Bk = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    b_ = biased_of("X2_d1")
+    for side in (1, -1):
+        got = run_biased(lib, torch, Bk, buf, 1, lib.CFD_OP_DX | lib.CFD_OP_DY | lib.CFD_OP_DZ, side, 1, prec=prec)
+        got = got.reshape(mesh.nblocks, 3, N, N, N)
+        want = B.biased_uniform(ext, b_, side, (dx, dx, dx), N, g, ("x", "y"), 1)
+        tol = TOL64 if prec == 0 else TOL_TC
+        for i, c in enumerate(("x", "y")):
+            assert rel_max(got[:, i], want[c].reshape(mesh.nblocks, N, N, N)) < tol, (side, c)
+        wz = np.moveaxis(B.global_periodic(np.moveaxis(fg, 0, 0), b_, side, dx), 0, 0)
+        gz = C.blocks_to_global(got[:, 2].reshape(1, 4, 4, N, N, N))
+        assert rel_max(gz, wz) < tol, (side, "z")
