@@ -33,6 +33,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 """
 from __future__ import annotations
 
+import functools
 from typing import Callable, List, Sequence, Tuple
 
 import mpmath as mp
@@ -194,10 +195,11 @@ def lsrk2s_rk4(dps: int = 50):
         return _unpack(x)
 
 
+@functools.lru_cache(maxsize=1)
 def lsrk2s_rk4_float():
-    """The same coefficients rounded to FP64 (the values the library receives)."""
+    """The same coefficients rounded to FP64 (the values the library receives); computed once."""
     g1, g2, b, d = lsrk2s_rk4()
-    return tuple([float(v) for v in arr] for arr in (g1, g2, b, d))
+    return tuple(tuple(float(v) for v in arr) for arr in (g1, g2, b, d))
 
 
 # ---------------------------------------------------------------------------
@@ -277,4 +279,30 @@ def advect_rhs(u, beta, b, dx3, N, g, n_iter, sigma, r):
 def advect_lsrk_step(u, beta, dt, coef, b, dx3, N, g, n_iter=0, sigma=0.0, r=4):
     """One 2S step of u_t = beta . grad u + sum_i Q_i[u]."""
     return lsrk2s_step((u,), dt, coef, lambda st: (advect_rhs(st[0], beta, b, dx3, N, g, n_iter, sigma, r),))[0]
+
+
+def advect_operator_1d(b, beta: float, n: int, dx: float, N: int, g: int, n_iter: int, sigma: float, r: int):
+    """Dense n x n matrix of u -> beta D u + Q u on a periodic line of n/N blocks: D the
+    decomposed biased operator upwinded for the right-hand-side term beta d_x (right-biased where
+    beta > 0, left-biased where beta < 0; oracle.biased.decomposed_1d with n_iter iterations), Q
+    the Kreiss-Oliger term (ko_1d).  Columns are the images of the unit vectors."""
+    from oracle import biased as B
+    side = -1 if beta > 0 else 1
+    I = np.eye(n)
+    D = B.decomposed_1d(I, b, side, dx, N, g, n_iter)
+    Q = np.stack([ko_1d(I[:, j], 0, r, sigma, dx) for j in range(n)], 1) if sigma > 0 else 0.0
+    return beta * D + Q
+
+
+def fully_discrete_2d(Mx: np.ndarray, My: np.ndarray, U0: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+    """nsteps of a 4-stage 4th-order Runge-Kutta method (every member advances a linear autonomous
+    system by R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, including the 2S method above) for
+    U_t = My U + U Mx^T, U indexed (y, x): in the eigenbases of Mx and My the operator is
+    diagonal with entries lam_y + lam_x, so U(n dt) = Vy [(Vy^-1 U0 Vx^-T) * R(dt(lam_y+lam_x))^n] Vx^T."""
+    lx, Vx = np.linalg.eig(Mx)
+    ly, Vy = np.linalg.eig(My)
+    Uh = np.linalg.solve(Vy, np.linalg.solve(Vx, U0.T).T)
+    z = dt * (ly[:, None] + lx[None, :])
+    R = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    return (Vy @ (Uh * R ** nsteps) @ Vx.T).real
 

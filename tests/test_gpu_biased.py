@@ -506,3 +506,45 @@ def test_biased_slab_mixed_cyclic_and_decomposed_axes(lib, torch, prec):
         wz = np.moveaxis(B.global_periodic(np.moveaxis(fg, 0, 0), b_, side, dx), 0, 0)
         gz = C.blocks_to_global(got[:, 2].reshape(1, 4, 4, N, N, N))
         assert rel_max(gz, wz) < tol, (side, "z")
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-6)])
+def test_advect_long_time_matches_the_fully_discrete_prediction(lib, torch, prec, tol):
+    """5000 2S steps of 2D advection (64^2 as 4 x 4 blocks of 16^2, one block thick in z; X_2 with
+    one iteration, dissipation, direction 30 degrees, CFL 1/10) on the GPU equal the oracle's
+    exact propagation of the same fully discrete linear system (eigen-basis form of R(dt L)^n):
+    a long-time check of the upwinding, the iteration, the dissipation and the step together."""
+    from oracle import timestep as T
+    from paper_2302_14858_gb300 import workloads as W
+    N, g, sigma, r, nsteps = 16, 4, 0.04, 4, 5000
+    NM = 64
+    mesh = W.periodic_box_mesh(4, 4, 1, N, g)
+    E = N + 2 * g
+    dx = 2 * np.pi / NM
+    c = (np.cos(np.pi / 6), np.sin(np.pi / 6))
+    b_ = biased_of("X2_d1")
+    x = (np.arange(NM) + 0.5) * dx
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    U0 = 0.05 * np.exp(-np.sin(2 * (X - 0.2))) * (np.exp(-1.5 * (Y - np.pi) ** 2) * (1.2 * np.sin(7 * Y) - np.cos(7 * Y))
+                                                  + np.sin(2 * Y - 1.0))
+    fg = np.broadcast_to(U0, (N, NM, NM)).copy()          # constant along z
+    buf = C.ghost_fill_3d(fg, N, g).reshape(mesh.nblocks, E, E, E).reshape(-1)
+    bb = np.empty((mesh.nblocks, 3, E, E, E))
+    bb[:, 0], bb[:, 1], bb[:, 2] = -c[0], -c[1], 0.0
+    Bk = bind(lib, "X2_d1", mesh, g, lib.CFD_F64)
+    tu = torch.from_numpy(buf).cuda()
+    tb = torch.from_numpy(bb.reshape(-1)).cuda()
+    work = torch.empty(lib.cfd_advect_lsrk_workspace(Bk, 1, prec, 1), dtype=torch.uint8, device="cuda")
+    coef = T.lsrk2s_rk4_float()
+    dt = 0.1 * dx
+    for _ in range(nsteps):
+        lib.cfd_advect_lsrk_step(Bk, tu, 1, tb, dt, coef, sigma, r, prec, 1, work)
+    lib.cfd_sync_status(Bk)
+    got = tu.cpu().numpy().reshape(1, 4, 4, E, E, E)[:, :, :, g:g + N, g:g + N, g:g + N]
+    got = C.blocks_to_global(got)                           # (z, y, x)
+    Mx = T.advect_operator_1d(b_, -c[0], NM, dx, N, g, 1, sigma, r)
+    My = T.advect_operator_1d(b_, -c[1], NM, dx, N, g, 1, sigma, r)
+    want = T.fully_discrete_2d(Mx, My, U0, dt, nsteps)
+    for zp in (0, N - 1):
+        assert rel_max(got[zp], want) < tol, (zp, rel_max(got[zp], want))
+

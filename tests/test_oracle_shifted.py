@@ -149,3 +149,28 @@ def test_advection_step_advances_a_mode_by_the_stability_polynomial():
     u0 = T.advect_lsrk_step(u, [0 * X] * 3, dt, T.lsrk2s_rk4_float(), b, (dx, dx, dx), N, g, n_iter, sigma, r)
     assert np.max(np.abs(u0 - u1)) > 1e-2 * np.max(np.abs(u))
 
+
+def test_fully_discrete_2d_equals_stepping():
+    """The eigen-basis propagation of fully_discrete_2d equals 300 explicit 2S steps of the same
+    semi-discrete 2D advection operator (decomposed X_2, one iteration, dissipation), and the
+    upwinded operator has no growing mode (|R| <= 1)."""
+    b = _biased("X2_d1")
+    NM, N, g, sigma, r = 64, 16, 4, 0.04, 4
+    dx = 2 * np.pi / NM
+    c = (np.cos(np.pi / 6), np.sin(np.pi / 6))
+    Mx = T.advect_operator_1d(b, -c[0], NM, dx, N, g, 1, sigma, r)
+    My = T.advect_operator_1d(b, -c[1], NM, dx, N, g, 1, sigma, r)
+    x = (np.arange(NM) + 0.5) * dx
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    U0 = np.sin(2 * X - Y) + 0.3 * np.cos(5 * Y + 1.0)
+    dt = 0.1 * dx
+    U = U0.copy()
+    coef = T.lsrk2s_rk4_float()
+    for _ in range(300):
+        U = T.lsrk2s_step((U,), dt, coef, lambda st: (st[0] @ Mx.T + My @ st[0],))[0]
+    Ue = T.fully_discrete_2d(Mx, My, U0, dt, 300)
+    assert np.abs(Ue - U).max() < 1e-12 * np.abs(U).max()
+    lam = np.add.outer(np.linalg.eigvals(My), np.linalg.eigvals(Mx)) * dt
+    R = 1 + lam + lam ** 2 / 2 + lam ** 3 / 6 + lam ** 4 / 24
+    assert np.abs(R).max() <= 1 + 1e-12
+
