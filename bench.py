@@ -1036,15 +1036,33 @@ def run_adv2d(args, spec):
     n_iter = spec["n_iter"]
     sigma, r = 0.04, 4
 
-    def run(prec, steps):
+    def run(prec, steps, graph=False):
         work = torch.empty(cfd.cfd_advect_lsrk_workspace(blocks, 1, prec, n_iter), dtype=torch.uint8, device=dev)
-        step = lambda: cfd.cfd_advect_lsrk_step(blocks, u, 1, beta, dt, coef, sigma, r, prec, n_iter, work, stream)
+        step = lambda st=stream: cfd.cfd_advect_lsrk_step(blocks, u, 1, beta, dt, coef, sigma, r, prec, n_iter,
+                                                          work, st)
         u.copy_(u0)
         for _ in range(args.warmup):
             step()
         u.copy_(u0)
         torch.cuda.synchronize()
-        ms = timed(step, steps, stream, torch)
+        if graph:
+            # G steps captured once into a CUDA graph (the launches of a small problem dominate)
+            G = 10
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(stream)
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=side):
+                cur = torch.cuda.current_stream(dev)
+                for _ in range(G):
+                    step(cur)
+            stream.wait_stream(side)
+            u.copy_(u0)
+            torch.cuda.synchronize()
+            reps = max(1, steps // G)
+            ms = timed(gr.replay, reps, torch.cuda.current_stream(dev), torch) / G
+            steps = reps * G
+        else:
+            ms = timed(step, steps, stream, torch)
         cfd.cfd_sync_status(blocks, stream)
         exact = field(steps * dt).view(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
         got = u.view(mesh.nblocks, E, E, E)[:, g:g + N, g:g + N, g:g + N]
@@ -1066,6 +1084,11 @@ def run_adv2d(args, spec):
         ms64, err64 = run(PREC["fp64_banded"], args.steps)
         compare = {"fp64_banded": {"steps_per_s": round(1e3 / ms64, 3), "ms_per_step": round(ms64, 4),
                                    "max_err_vs_exact": err64}, "speedup_vs_fp64_banded": round(ms64 / ms, 3)}
+    graph = None
+    if args.graph:
+        msg, errg = run(prec, args.steps, graph=True)
+        graph = {"steps_per_s": round(1e3 / msg, 3), "ms_per_step": round(msg, 5), "max_err_vs_exact": errg,
+                 "value": round(whole_job_value(units, world, msg), 4), "steps_per_graph": 10}
     cpu = cpu_baseline(spec) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         line = {
@@ -1078,7 +1101,7 @@ def run_adv2d(args, spec):
                        "grid": [NM, NM], "block": N, "angle_deg": spec["angle_deg"], "cfl": spec["cfl"],
                        "ko": {"sigma": sigma, "r": r}, "parallelism": f"replicas x{world}"},
             "steps_per_s": round(1e3 / ms * world, 3), "t_final": args.steps * dt, "max_err_vs_exact": err,
-            "compare": compare, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
+            "compare": compare, "graph": graph, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line))
     if world > 1:
