@@ -904,11 +904,12 @@ def run_advect(args, spec):
     if prec != cfd.CFD_FP64_BANDED:
         # k_dense: per axis the field is read once and both biased derivatives written once; each
         # halo-only pass of the iteration reads the field again.  The blend kernel reads the
-        # upwind derivative of each axis and the three shift components, and writes the term.
+        # upwind derivative of each axis per field, the three shift components once per point,
+        # and writes the term.
         elem = fields.element_size()
         per_pf = 3 * (3 + n_iter) * elem
         ach = per_pf * units * prof_steps / (tdl * 1e-3) / 1e9
-        comb_b = (3 + 3 + 1) * elem * units * prof_steps
+        comb_b = (3 + 1 + 3 / nf) * elem * units * prof_steps
         roof = {"kernel": "k_dense (tcgen05 BF16 digit-slice GEMM, biased operators D+ and D-)", "bound": "hbm",
                 "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",

@@ -507,7 +507,9 @@ cfd_status check_work(cfd_blocks_s *B, int nf, cfd_precision prec, int n_iter, v
 }
 
 // Upwind blend of the two biased derivatives of every axis (tensor-core path): one thread per
-// interior point of one (block, field); axes added in the order x, y, z.
+// interior point of one block, looping over the fields (the shift is read once per point);
+// axes added in the order x, y, z, in the field precision (FP32 fields in FP32: GB300's FP64
+// pipe, not memory, bounded this kernel when FP32 values were widened to FP64).
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_advect_combine(const T *__restrict__ tmp, const T *__restrict__ beta, T *out,
                                  const int *__restrict__ blocks, const long long *__restrict__ extpre,
@@ -517,29 +519,49 @@ __global__ void __launch_bounds__(256) k_advect_combine(const T *__restrict__ tm
   const int n3 = N * N * N;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n3) return;
-  const int job = blockIdx.y;
-  const int lb = job / nf, q = job - lb * nf;
-  const int b = blocks[lb];
+  const int b = blocks[blockIdx.y];
   const int x = i % N, y = (i / N) % N, z = i / (N * N);
   const int E = N + 2 * g;
   const long long E3 = (long long)E * E * E;
   const T *bt = beta + 3 * extpre[b] + ((long long)(z + g) * E + (y + g)) * E + (x + g);
-  const T *tp = tmp + (long long)nf * 6 * intpre[b] + (long long)q * 6 * n3 + i;
-  T *o = out + (long long)nf * out_nops * intpre[b] + ((long long)q * out_nops + out_opidx) * n3 + i;
-  // all loads issued before any use: the three shift components, then one derivative per axis
-  // (beta > 0: the right-biased one, slot 2c+1; beta < 0: the left-biased one, slot 2c)
-  T bv[3], dv[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) bv[c] = __ldg(bt + c * E3);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dv[c] = __ldg(tp + (2 * c + (sign_bits(bv[c]) == 1 ? 1 : 0)) * (long long)n3);
-  double acc = accum_all ? static_cast<double>(*o) : 0.0;
+  // the shift and, per axis, which biased derivative it takes: beta > 0 the right-biased one
+  // (slot 2c+1), beta < 0 the left-biased one (slot 2c), beta = 0 none
+  T bv[3];
+  int slot[3], sg[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double t = sign_bits(bv[c]) == 0 ? 0.0 : static_cast<double>(bv[c]) * static_cast<double>(dv[c]);
-    acc = (c == 0 && !accum_all) ? t : acc + t;
+    bv[c] = __ldg(bt + c * E3);
+    sg[c] = sign_bits(bv[c]);
+    slot[c] = 2 * c + (sg[c] == 1 ? 1 : 0);
   }
-  *o = static_cast<T>(acc);
+  const T *tp = tmp + (long long)nf * 6 * intpre[b] + i;
+  T *o = out + (long long)nf * out_nops * intpre[b] + (long long)out_opidx * n3 + i;
+  // fields in groups of QB, every load of a group issued before its first store
+  constexpr int QB = 4;
+  for (int q0 = 0; q0 < nf; q0 += QB) {
+    T dv[QB][3], prev[QB];
+#pragma unroll
+    for (int u = 0; u < QB; ++u) {
+      prev[u] = T(0);
+      if (q0 + u < nf) {
+        const T *tq = tp + (long long)(q0 + u) * 6 * n3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dv[u][c] = __ldg(tq + (long long)slot[c] * n3);
+        if (accum_all) prev[u] = o[(long long)(q0 + u) * out_nops * n3];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < QB; ++u) {
+      if (q0 + u >= nf) break;
+      T acc = prev[u];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T t = sg[c] == 0 ? T(0) : bv[c] * dv[u][c];
+        acc = (c == 0 && !accum_all) ? t : acc + t;
+      }
+      o[(long long)(q0 + u) * out_nops * n3] = acc;
+    }
+  }
 }
 
 }  // namespace
@@ -549,7 +571,7 @@ cfd_status advect_combine(cfd_blocks_s *B, const void *tmp6, const void *beta, i
   for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
     const int N = B->sizes[gi];
     const int n3 = N * N * N;
-    dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)(B->groups[gi].size() * nf));
+    dim3 grid((unsigned)((n3 + 255) / 256), (unsigned)B->groups[gi].size());
     launch_begin(KF_BIASED, st);
     auto go = [&](auto tag, auto nc) {
       using T = decltype(tag);

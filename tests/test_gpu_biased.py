@@ -216,6 +216,65 @@ def test_advect_parity(lib, torch, name, g, n_iter, shift, prec):
         assert rel_max(got[:, q], want) < (TOL64 if prec == 0 else TOL_TC)
 
 
+def test_advect_many_fields_tc(lib, torch):
+    """Six fields on the tensor cores (the blend handles fields in groups of four, the second
+    group partial): every field against the FP64 banded path, the first and last against the oracle."""
+    NM, N, g, nf, name = 64, 16, 4, 6, "X2_d1"
+    fields = case_fields(23, nf)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    _, _, bexts, bbuf = uniform_case(NM, N, g, shift_fields())
+    blocks = bind(lib, name, mesh, g, lib.CFD_F64)
+    dev = torch.device("cuda", 0)
+    f_t = torch.from_numpy(buf).to(dev)
+    b_t = torch.from_numpy(bbuf).to(dev)
+    outs = []
+    for prec in (0, 2):
+        out = torch.zeros(mesh.nblocks * nf * N ** 3, dtype=torch.float64, device=dev)
+        ws = lib.cfd_biased_workspace(blocks, nf, prec, 1)
+        work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+        lib.cfd_advect(blocks, f_t, nf, b_t, prec, 1, out, work)
+        lib.cfd_sync_status(blocks)
+        outs.append(out.cpu().numpy().reshape(mesh.nblocks, nf, N, N, N))
+    assert rel_max(outs[1], outs[0]) < TOL_TC
+    I = slice(g, g + N)
+    beta = [e[:, :, :, I, I, I] for e in bexts]
+    b = biased_of(name)
+    for q in (0, nf - 1):
+        want = B.advect_uniform(exts[q], beta, b, (dx, dx, dx), N, g, 1).reshape(mesh.nblocks, N, N, N)
+        assert rel_max(outs[0][:, q], want) < TOL64
+        assert rel_max(outs[1][:, q], want) < TOL_TC
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_advect_float32_fields(lib, torch, prec):
+    """FP32 fields and shift (5 fields: the tensor-core blend's second group of four is partial),
+    within 2e-6 of the oracle's FP64 result on the same rounded inputs."""
+    NM, N, g, nf, name = 64, 16, 4, 5, "X2_d1"
+    fields = case_fields(27, nf)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    _, _, bexts, bbuf = uniform_case(NM, N, g, shift_fields())
+    buf32, bbuf32 = buf.astype(np.float32), bbuf.astype(np.float32)
+    blocks = bind(lib, name, mesh, g, lib.CFD_F32)
+    dev = torch.device("cuda", 0)
+    f_t = torch.from_numpy(buf32).to(dev)
+    b_t = torch.from_numpy(bbuf32).to(dev)
+    out = torch.zeros(mesh.nblocks * nf * N ** 3, dtype=torch.float32, device=dev)
+    ws = lib.cfd_biased_workspace(blocks, nf, prec, 1)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    lib.cfd_advect(blocks, f_t, nf, b_t, prec, 1, out, work)
+    lib.cfd_sync_status(blocks)
+    got = out.cpu().numpy().astype(np.float64).reshape(mesh.nblocks, nf, N, N, N)
+    E = N + 2 * g
+    I = slice(g, g + N)
+    b32 = bbuf32.reshape(mesh.nblocks, 3, E, E, E).astype(np.float64)
+    beta = [b32[:, i].reshape(bexts[i].shape)[:, :, :, I, I, I] for i in range(3)]
+    b = biased_of(name)
+    for q in range(nf):
+        ext = buf32.reshape(mesh.nblocks, nf, E, E, E)[:, q].astype(np.float64).reshape(exts[q].shape)
+        want = B.advect_uniform(ext, beta, b, (dx, dx, dx), N, g, 1).reshape(mesh.nblocks, N, N, N)
+        assert rel_max(got[:, q], want) < 2e-6
+
+
 def test_rejections(lib, torch):
     NM, N, g = 32, 16, 4
     fields = case_fields(1, 1)
