@@ -527,12 +527,13 @@ __global__ void __launch_bounds__(256) k_advect_combine(const T *__restrict__ tm
   // the shift and, per axis, which biased derivative it takes: beta > 0 the right-biased one
   // (slot 2c+1), beta < 0 the left-biased one (slot 2c), beta = 0 none
   T bv[3];
-  int slot[3], sg[3];
+  int slot[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     bv[c] = __ldg(bt + c * E3);
-    sg[c] = sign_bits(bv[c]);
-    slot[c] = 2 * c + (sg[c] == 1 ? 1 : 0);
+    const int sg = sign_bits(bv[c]);
+    slot[c] = 2 * c + (sg == 1 ? 1 : 0);
+    if (sg == 0) bv[c] = T(0);  // a zero shift adds nothing (+0 times a finite derivative)
   }
   const T *tp = tmp + (long long)nf * 6 * intpre[b] + i;
   T *o = out + (long long)nf * out_nops * intpre[b] + (long long)out_opidx * n3 + i;
@@ -550,15 +551,13 @@ __global__ void __launch_bounds__(256) k_advect_combine(const T *__restrict__ tm
         if (accum_all) prev[u] = o[(long long)(q0 + u) * out_nops * n3];
       }
     }
+    // x, y, z as one FMA chain (three FP64-pipe operations per point and field for FP64 fields)
 #pragma unroll
     for (int u = 0; u < QB; ++u) {
       if (q0 + u >= nf) break;
-      T acc = prev[u];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T t = sg[c] == 0 ? T(0) : bv[c] * dv[u][c];
-        acc = (c == 0 && !accum_all) ? t : acc + t;
-      }
+      T acc = accum_all ? fma(bv[0], dv[u][0], prev[u]) : bv[0] * dv[u][0];
+      acc = fma(bv[1], dv[u][1], acc);
+      acc = fma(bv[2], dv[u][2], acc);
       o[(long long)(q0 + u) * out_nops * n3] = acc;
     }
   }
