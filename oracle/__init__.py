@@ -32,8 +32,9 @@ biased    Biased first-degree schemes: UCD slow/fast U_M, V_M (Eq.
           counterpart), their iteration (Eq. iter_left_X) and the upwinded
           shift-advection term (Eq. biasderapproxadv).
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
-the 3D mixed-derivative path with hybrid iteration (``apply3d`` with
-``n_iter > 0`` and a mixed op), whose pin is only partial (tensor-product
-consistency and the iteration fixed point; parity unpinned beyond that).
+Parity status: every function is pinned by ``tests/test_oracle_*.py``.  The 3D
+path (``apply_uniform``, mixed ops and hybrid iteration included) is pinned on
+separable and on general random data against the decomposed 1D operator applied
+to global lines, which is itself pinned against the dense embedded operator
+[i]D of Eq. iter_scheme.
 """

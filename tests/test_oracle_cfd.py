@@ -214,6 +214,33 @@ def test_3d_tensor_product_consistency(n_iter):
         assert np.abs(got - want[op]).max() <= 1e-12 * np.abs(want[op]).max(), op
 
 
+@pytest.mark.parametrize("n_iter", [0, 1, 2])
+def test_3d_general_data_equals_line_operators(n_iter):
+    """Random (non-separable) data: every 3D op equals the decomposed 1D operator applied to the
+    global lines, the mixed ones as (D_i[D_j f] + D_j[D_i f]) / 2 of those line operators.  The
+    separable test above pins the 3D path on tensor-product data only; a mistake that cancels
+    there (ghost rows of the intermediate, the iterate a block reads across an edge) fails here."""
+    NM, N, g = 32, 8, 4
+    r = np.random.default_rng(77 + n_iter)
+    fg = r.standard_normal((NM, NM, NM))
+    dx = 2 * np.pi / NM
+    res = C.apply_uniform(C.ghost_fill_3d(fg, N, g), Q1, Q2, (dx, dx, dx), N, g, C.OPS, n_iter)
+
+    def line(f, s, axis):           # axis 0 z, 1 y, 2 x of the global array
+        return np.moveaxis(C.decomposed_1d(np.moveaxis(f, axis, 0), s, dx, N, g, n_iter), 0, axis)
+
+    ax = {"x": 2, "y": 1, "z": 0}
+    want = {}
+    for a in "xyz":
+        want["d" + a] = line(fg, Q1, ax[a])
+        want["d" + a + a] = line(fg, Q2, ax[a])
+    for a, b in (("x", "y"), ("x", "z"), ("y", "z")):
+        want["d" + a + b] = 0.5 * (line(want["d" + b], Q1, ax[a]) + line(want["d" + a], Q1, ax[b]))
+    for op in C.OPS:
+        got = C.blocks_to_global(res[op])
+        assert np.abs(got - want[op]).max() <= 1e-12 * np.abs(want[op]).max(), op
+
+
 def test_mixed_orders_agree_without_iteration():
     """With closures only, D_i D_j and D_j D_i are the same Kronecker operator (rounding aside)."""
     NM, N, g = 32, 8, 4
