@@ -153,6 +153,7 @@ void cfd_blocks_destroy(cfd_blocks_t blocks);
  * direction with a neighbour >= 0, copy the neighbour's interior slab into
  * the block's ghost region (faces, edges and corners).  `fields` is the
  * device field buffer described above with `nfields` fields.  Exact copy.
+ * CFD_ERR_UNSUPPORTED when the blocks of one size times nfields exceed 65535.
  */
 cfd_status cfd_exchange_ghosts(cfd_blocks_t blocks, void *fields, int nfields, void *stream);
 

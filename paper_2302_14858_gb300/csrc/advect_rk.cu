@@ -121,6 +121,11 @@ extern "C" cfd_status cfd_advect_lsrk_step(cfd_blocks_t B, void *u, int nfields,
     return CFD_ERR_ARG;
   }
   if (B->dtype != CFD_F64) { set_error("cfd_advect_lsrk_step: FP64 fields only"); return CFD_ERR_UNSUPPORTED; }
+  for (auto &grp : B->groups)
+    if ((long long)grp.size() * nfields > 65535) {
+      set_error("cfd_advect_lsrk_step: blocks of one size x nfields exceeds 65535");
+      return CFD_ERR_UNSUPPORTED;
+    }
   for (int v : B->nbr)
     if (v < 0) { set_error("cfd_advect_lsrk_step: every ghost region needs a neighbour"); return CFD_ERR_UNSUPPORTED; }
   size_t need = 0;

@@ -267,6 +267,11 @@ cfd_status launch_line(const LineParams &P, const LineTables &T, cudaStream_t st
 }
 
 cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nf, cudaStream_t st) {
+  for (auto &grp : B->groups)
+    if ((long long)grp.size() * nf > 65535) {  // (block, field) pairs of one size go in gridDim.y
+      set_error("ghost exchange: blocks of one size x nfields exceeds 65535");
+      return CFD_ERR_UNSUPPORTED;
+    }
   for (size_t gi = 0; gi < B->sizes.size(); ++gi) {
     const int N = B->sizes[gi];
     const int nblk = (int)B->groups[gi].size();
