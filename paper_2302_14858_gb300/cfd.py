@@ -51,12 +51,14 @@ KERNEL_FAMILIES = {"exchange": 0, "line": 1, "rk_combine": 2, "dense": 3, "dense
 
 
 class CfdError(RuntimeError):
+    """A call that returned a status other than CFD_OK (status and the library's message)."""
     def __init__(self, status: int, msg: str):
         super().__init__(f"cfd status {status}: {msg}")
         self.status = status
 
 
 class SchemeDesc(ctypes.Structure):
+    """cfd_scheme_desc: one centred tridiagonal scheme of one derivative degree."""
     _fields_ = [("deriv", c_int), ("order", c_int), ("M", c_int), ("lhs_offdiag", c_double),
                 ("rhs", POINTER(c_double)), ("closure_halfwidth", c_int), ("closure", POINTER(c_double))]
 
@@ -87,6 +89,7 @@ _lib.cfd_wave_rk_step.restype = c_int
 
 
 class LsrkDesc(ctypes.Structure):
+    """cfd_lsrk_desc: the coefficients of a two-register (2S) low-storage RK method."""
     _fields_ = [("stages", c_int), ("gamma1", POINTER(c_double)), ("gamma2", POINTER(c_double)),
                 ("beta", POINTER(c_double)), ("delta", POINTER(c_double))]
 
@@ -99,6 +102,7 @@ _lib.cfd_wave_lsrk_step.restype = c_int
 
 
 class BiasedDesc(ctypes.Structure):
+    """cfd_biased_desc: a left-biased first-degree scheme with its closure."""
     _fields_ = [("order", c_int), ("a", c_double), ("rhs_lo", c_int), ("rhs_n", c_int), ("rhs", POINTER(c_double)),
                 ("closure_sup", c_double), ("closure_lo", c_int), ("closure_n", c_int),
                 ("closure", POINTER(c_double)), ("kc", c_int)]
@@ -147,6 +151,7 @@ _lib.cfd_last_error.restype = ctypes.c_char_p
 
 
 def cfd_last_error() -> str:
+    """Message of the last failed call on this thread."""
     return _lib.cfd_last_error().decode()
 
 
@@ -161,6 +166,17 @@ def _ptr(x) -> Optional[int]:
     if isinstance(x, int):
         return x
     return x.data_ptr()
+
+
+def _nbytes(work, work_bytes=None) -> int:
+    """Size of a workspace: a tensor's own size, or `work_bytes` for a raw device address."""
+    if work is None:
+        return 0
+    if work_bytes is not None:
+        return int(work_bytes)
+    if isinstance(work, int):
+        raise ValueError("a workspace given as a raw device address needs work_bytes")
+    return work.numel() * work.element_size()
 
 
 def _stream(s) -> Optional[int]:
@@ -226,6 +242,7 @@ def cfd_scheme_create(first: Optional[dict], second: Optional[dict]) -> Scheme:
 
 
 def cfd_scheme_closure(scheme: Scheme, deriv: int):
+    """The closure coefficients the scheme uses for degree `deriv` (given or C_0-matched)."""
     buf = (c_double * 13)()
     hw = c_int()
     _check(_lib.cfd_scheme_closure(scheme.handle, deriv, buf, ctypes.byref(hw)))
@@ -233,6 +250,7 @@ def cfd_scheme_closure(scheme: Scheme, deriv: int):
 
 
 def cfd_blocks_bind(scheme: Scheme, block_n: Sequence[int], dx, neighbors, ng: int, dtype: int) -> Blocks:
+    """Bind a scheme to a MeshBlock layout: per-block sizes, spacings and 26 neighbours (-1: none)."""
     import numpy as np
     nb = len(block_n)
     n_arr = (c_int * nb)(*[int(v) for v in block_n])
@@ -245,20 +263,22 @@ def cfd_blocks_bind(scheme: Scheme, block_n: Sequence[int], dx, neighbors, ng: i
 
 
 def cfd_exchange_ghosts(blocks: Blocks, fields, nfields: int, stream=None):
+    """Ghost fill of every block from its neighbours (matrix G, Eq. example_G)."""
     _check(_lib.cfd_exchange_ghosts(blocks.handle, _ptr(fields), nfields, _stream(stream)))
 
 
 def cfd_apply_workspace(blocks: Blocks, nfields: int, op_mask: int, prec: int, n_iter: int) -> int:
+    """Device workspace bytes cfd_apply needs for this request."""
     n = c_size_t()
     _check(_lib.cfd_apply_workspace(blocks.handle, nfields, op_mask, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 
 def cfd_apply(blocks: Blocks, fields, nfields: int, op_mask: int, prec: int, n_iter: int, out, work,
-              stream=None):
-    nbytes = 0 if work is None else (work.numel() * work.element_size() if hasattr(work, "numel") else 1 << 62)
+              stream=None, work_bytes=None):
+    """The requested derivatives of every field (Eq. sch_cent_om closed, Eq. iter_center_P iterated)."""
     _check(_lib.cfd_apply(blocks.handle, _ptr(fields), nfields, op_mask, prec, n_iter, _ptr(out), _ptr(work),
-                          nbytes, _stream(stream)))
+                          _nbytes(work, work_bytes), _stream(stream)))
 
 
 def cfd_apply_static(blocks: Blocks, fields, nfields: int, op_mask: int, out, stream=None):
@@ -271,25 +291,28 @@ def cfd_apply_static(blocks: Blocks, fields, nfields: int, op_mask: int, out, st
 
 
 def cfd_wave_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
+    """Device workspace bytes of cfd_wave_rk_step."""
     n = c_size_t()
     _check(_lib.cfd_wave_workspace(blocks.handle, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 
-def cfd_wave_rk_step(blocks: Blocks, phi, K, dt: float, prec: int, n_iter: int, work, stream=None):
-    nbytes = work.numel() * work.element_size()
-    _check(_lib.cfd_wave_rk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), prec, n_iter, _ptr(work), nbytes,
-                                 _stream(stream)))
+def cfd_wave_rk_step(blocks: Blocks, phi, K, dt: float, prec: int, n_iter: int, work, stream=None,
+                     work_bytes=None):
+    """One classical RK4 step of Phi_t = K, K_t = sum_i D2_i Phi, in place."""
+    _check(_lib.cfd_wave_rk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), prec, n_iter, _ptr(work),
+                                 _nbytes(work, work_bytes), _stream(stream)))
 
 
 def cfd_wave_lsrk_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
+    """Device workspace bytes of cfd_wave_lsrk_step."""
     n = c_size_t()
     _check(_lib.cfd_wave_lsrk_workspace(blocks.handle, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 
 def cfd_wave_lsrk_step(blocks: Blocks, phi, K, dt: float, coef, sigma: float, ko_r: int, prec: int, n_iter: int,
-                       work, stream=None):
+                       work, stream=None, work_bytes=None):
     """coef = (gamma1, gamma2, beta, delta), sequences of equal length (the 2S coefficients)."""
     g1, g2, be, de = (list(map(float, c)) for c in coef)
     m = len(be)
@@ -297,9 +320,8 @@ def cfd_wave_lsrk_step(blocks: Blocks, phi, K, dt: float, coef, sigma: float, ko
         raise ValueError("the four coefficient sequences need the same length")
     arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
     desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
-    nbytes = work.numel() * work.element_size()
     _check(_lib.cfd_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), ctypes.byref(desc), float(sigma),
-                                   int(ko_r), prec, n_iter, _ptr(work), nbytes, _stream(stream)))
+                                   int(ko_r), prec, n_iter, _ptr(work), _nbytes(work, work_bytes), _stream(stream)))
 
 
 def cfd_scheme_set_biased(scheme: Scheme, d: dict):
@@ -315,34 +337,36 @@ def cfd_scheme_set_biased(scheme: Scheme, d: dict):
 
 
 def cfd_biased_workspace(blocks: Blocks, nfields: int, prec: int, n_iter: int) -> int:
+    """Device workspace bytes of cfd_apply_biased / cfd_advect."""
     n = c_size_t()
     _check(_lib.cfd_biased_workspace(blocks.handle, nfields, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 
-def _nbytes(work) -> int:
-    return 0 if work is None else work.numel() * work.element_size()
-
-
 def cfd_apply_biased(blocks: Blocks, fields, nfields: int, axis_mask: int, side: int, prec: int, n_iter: int, out,
-                     work=None, stream=None):
+                     work=None, stream=None, work_bytes=None):
+    """Biased first derivatives along the masked axes: side +1 left-biased S+, -1 right-biased S-
+    (Eqs. closure_left_X, iter_left_X and their mirrors)."""
     _check(_lib.cfd_apply_biased(blocks.handle, _ptr(fields), nfields, axis_mask, side, prec, n_iter, _ptr(out),
-                                 _ptr(work), _nbytes(work), _stream(stream)))
+                                 _ptr(work), _nbytes(work, work_bytes), _stream(stream)))
 
 
-def cfd_advect(blocks: Blocks, fields, nfields: int, beta, prec: int, n_iter: int, out, work=None, stream=None):
+def cfd_advect(blocks: Blocks, fields, nfields: int, beta, prec: int, n_iter: int, out, work=None, stream=None,
+               work_bytes=None):
+    """The upwinded shift-advection term sum_i beta^i d_i f of every field (Eq. biasderapproxadv)."""
     _check(_lib.cfd_advect(blocks.handle, _ptr(fields), nfields, _ptr(beta), prec, n_iter, _ptr(out), _ptr(work),
-                           _nbytes(work), _stream(stream)))
+                           _nbytes(work, work_bytes), _stream(stream)))
 
 
 def cfd_shifted_wave_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
+    """Device workspace bytes of cfd_shifted_wave_lsrk_step."""
     n = c_size_t()
     _check(_lib.cfd_shifted_wave_workspace(blocks.handle, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 
 def cfd_shifted_wave_lsrk_step(blocks: Blocks, phi, K, beta, dt: float, coef, sigma: float, ko_r: int, prec: int,
-                               n_iter: int, work, stream=None):
+                               n_iter: int, work, stream=None, work_bytes=None):
     """As cfd_wave_lsrk_step with the upwinded shift terms; beta = three fields in the field layout."""
     g1, g2, be, de = (list(map(float, c)) for c in coef)
     m = len(be)
@@ -352,17 +376,18 @@ def cfd_shifted_wave_lsrk_step(blocks: Blocks, phi, K, beta, dt: float, coef, si
     desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
     _check(_lib.cfd_shifted_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), _ptr(beta), float(dt),
                                            ctypes.byref(desc), float(sigma), int(ko_r), prec, n_iter, _ptr(work),
-                                           _nbytes(work), _stream(stream)))
+                                           _nbytes(work, work_bytes), _stream(stream)))
 
 
 def cfd_advect_lsrk_workspace(blocks: Blocks, nfields: int, prec: int, n_iter: int) -> int:
+    """Device workspace bytes of cfd_advect_lsrk_step."""
     n = c_size_t()
     _check(_lib.cfd_advect_lsrk_workspace(blocks.handle, nfields, prec, n_iter, ctypes.byref(n)))
     return n.value
 
 
 def cfd_advect_lsrk_step(blocks: Blocks, u, nfields: int, beta, dt: float, coef, sigma: float, ko_r: int, prec: int,
-                         n_iter: int, work, stream=None):
+                         n_iter: int, work, stream=None, work_bytes=None):
     """2S step of u_t = beta . grad u (+ Kreiss-Oliger) for nfields fields; coef = (gamma1, gamma2, beta, delta)."""
     g1, g2, be, de = (list(map(float, c)) for c in coef)
     m = len(be)
@@ -371,7 +396,7 @@ def cfd_advect_lsrk_step(blocks: Blocks, u, nfields: int, beta, dt: float, coef,
     arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
     desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
     _check(_lib.cfd_advect_lsrk_step(blocks.handle, _ptr(u), nfields, _ptr(beta), float(dt), ctypes.byref(desc),
-                                     float(sigma), int(ko_r), prec, n_iter, _ptr(work), _nbytes(work),
+                                     float(sigma), int(ko_r), prec, n_iter, _ptr(work), _nbytes(work, work_bytes),
                                      _stream(stream)))
 
 
@@ -399,28 +424,34 @@ def cfd_halo_plan_create(blocks: Blocks, items) -> HaloPlan:
 
 
 def cfd_halo_plan_bytes(plan: HaloPlan, nfields: int) -> int:
+    """Bytes of the contiguous buffer that holds the plan's slabs for nfields fields."""
     n = c_size_t()
     _check(_lib.cfd_halo_plan_bytes(plan.handle, nfields, ctypes.byref(n)))
     return n.value
 
 
 def cfd_halo_pack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
+    """Copy the plan's interior slabs of every field into `buf` (plan order)."""
     _check(_lib.cfd_halo_pack(plan.handle, _ptr(fields), nfields, _ptr(buf), _stream(stream)))
 
 
 def cfd_halo_unpack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
+    """Write `buf` (plan order) into the plan's ghost regions of every field."""
     _check(_lib.cfd_halo_unpack(plan.handle, _ptr(fields), nfields, _ptr(buf), _stream(stream)))
 
 
 def cfd_sync_status(blocks: Blocks, stream=None):
+    """Synchronise the stream and raise a status latched on the device (e.g. a bounded wait that ran out)."""
     _check(_lib.cfd_sync_status(blocks.handle, _stream(stream)))
 
 
 def cfd_kernel_launches() -> int:
+    """Kernels this library has launched in the process so far."""
     return int(_lib.cfd_kernel_launches())
 
 
 def cfd_profile_enable(on: bool):
+    """Turn per-launch CUDA-event timing of the kernel families on or off."""
     _check(_lib.cfd_profile_enable(1 if on else 0))
 
 
@@ -433,6 +464,7 @@ def cfd_profile_read(family: int):
 
 
 def op_mask(ops: Sequence[str]) -> int:
+    """Bit mask of the named ops (dx ... dyz)."""
     m = 0
     for o in ops:
         m |= OP_BITS[o]
@@ -440,4 +472,5 @@ def op_mask(ops: Sequence[str]) -> int:
 
 
 def ops_in_mask(mask: int):
+    """Names of the ops in a bit mask, in output order."""
     return [o for o in OPS if mask & OP_BITS[o]]

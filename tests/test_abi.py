@@ -86,3 +86,12 @@ def test_bind_rejects_bad_layout(cfd):
     n[1] = 32                                     # neighbour of a different size
     with pytest.raises(cfd.CfdError):
         cfd.cfd_blocks_bind(s, n, m.dx, m.neighbors, 4, cfd.CFD_F64)
+
+
+def test_workspace_size_of_a_raw_address_must_be_given(cfd):
+    """A workspace passed as a raw device address carries no size: the binding asks for it
+    instead of reporting an unchecked one to the library."""
+    assert cfd._nbytes(None) == 0
+    assert cfd._nbytes(0x7F0000000000, 4096) == 4096
+    with pytest.raises(ValueError):
+        cfd._nbytes(0x7F0000000000)
