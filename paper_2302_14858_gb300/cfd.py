@@ -311,15 +311,21 @@ def cfd_wave_lsrk_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
     return n.value
 
 
-def cfd_wave_lsrk_step(blocks: Blocks, phi, K, dt: float, coef, sigma: float, ko_r: int, prec: int, n_iter: int,
-                       work, stream=None, work_bytes=None):
-    """coef = (gamma1, gamma2, beta, delta), sequences of equal length (the 2S coefficients)."""
+def _lsrk_desc(coef):
+    """cfd_lsrk_desc of coef = (gamma1, gamma2, beta, delta), sequences of equal length; the
+    arrays it points to are returned beside it and must stay alive for the call."""
     g1, g2, be, de = (list(map(float, c)) for c in coef)
     m = len(be)
     if not (len(g1) == len(g2) == len(de) == m):
         raise ValueError("the four coefficient sequences need the same length")
     arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
-    desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
+    return LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs]), arrs
+
+
+def cfd_wave_lsrk_step(blocks: Blocks, phi, K, dt: float, coef, sigma: float, ko_r: int, prec: int, n_iter: int,
+                       work, stream=None, work_bytes=None):
+    """coef = (gamma1, gamma2, beta, delta), sequences of equal length (the 2S coefficients)."""
+    desc, _keep = _lsrk_desc(coef)
     _check(_lib.cfd_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), float(dt), ctypes.byref(desc), float(sigma),
                                    int(ko_r), prec, n_iter, _ptr(work), _nbytes(work, work_bytes), _stream(stream)))
 
@@ -368,12 +374,7 @@ def cfd_shifted_wave_workspace(blocks: Blocks, prec: int, n_iter: int) -> int:
 def cfd_shifted_wave_lsrk_step(blocks: Blocks, phi, K, beta, dt: float, coef, sigma: float, ko_r: int, prec: int,
                                n_iter: int, work, stream=None, work_bytes=None):
     """As cfd_wave_lsrk_step with the upwinded shift terms; beta = three fields in the field layout."""
-    g1, g2, be, de = (list(map(float, c)) for c in coef)
-    m = len(be)
-    if not (len(g1) == len(g2) == len(de) == m):
-        raise ValueError("the four coefficient sequences need the same length")
-    arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
-    desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
+    desc, _keep = _lsrk_desc(coef)
     _check(_lib.cfd_shifted_wave_lsrk_step(blocks.handle, _ptr(phi), _ptr(K), _ptr(beta), float(dt),
                                            ctypes.byref(desc), float(sigma), int(ko_r), prec, n_iter, _ptr(work),
                                            _nbytes(work, work_bytes), _stream(stream)))
@@ -389,12 +390,7 @@ def cfd_advect_lsrk_workspace(blocks: Blocks, nfields: int, prec: int, n_iter: i
 def cfd_advect_lsrk_step(blocks: Blocks, u, nfields: int, beta, dt: float, coef, sigma: float, ko_r: int, prec: int,
                          n_iter: int, work, stream=None, work_bytes=None):
     """2S step of u_t = beta . grad u (+ Kreiss-Oliger) for nfields fields; coef = (gamma1, gamma2, beta, delta)."""
-    g1, g2, be, de = (list(map(float, c)) for c in coef)
-    m = len(be)
-    if not (len(g1) == len(g2) == len(de) == m):
-        raise ValueError("the four coefficient sequences need the same length")
-    arrs = [(c_double * m)(*v) for v in (g1, g2, be, de)]
-    desc = LsrkDesc(m, *[ctypes.cast(a, POINTER(c_double)) for a in arrs])
+    desc, _keep = _lsrk_desc(coef)
     _check(_lib.cfd_advect_lsrk_step(blocks.handle, _ptr(u), nfields, _ptr(beta), float(dt), ctypes.byref(desc),
                                      float(sigma), int(ko_r), prec, n_iter, _ptr(work), _nbytes(work, work_bytes),
                                      _stream(stream)))
