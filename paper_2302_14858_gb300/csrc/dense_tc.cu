@@ -1188,6 +1188,10 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
   size_t need = 0;
   cfd_status s = dense_workspace(B, nf, mask, prec, n_iter, &need);
   if (s != CFD_OK) return s;
+  if (need > 256 && (!work || work_bytes < need)) {
+    set_error("dense: workspace too small (see cfd_apply_workspace)");
+    return CFD_ERR_ARG;
+  }
   DenseState *ds = state_of(B);
   if (!ds) { set_error("dense: operators were not built at bind"); return CFD_ERR_UNSUPPORTED; }
   const int S = slices_of(prec), L = levels_of(prec);
