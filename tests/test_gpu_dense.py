@@ -185,9 +185,9 @@ def test_exact_slices_single_periodic_block(lib, torch):
     assert rel_max(got[1], np.moveaxis(want_dyy, 0, 1)) < TOL_EXACT64
 
 
-def test_exact_slices_fp32_uneven_blocks(lib, torch):
-    """Blocks of 16^3 and 32^3 with analytic ghosts on the level interface, FP32 fields."""
-    # 16^3 coarse blocks with a 2:1 refined octant of 32^3 blocks (both sizes run on the tensor cores)
+def box16_32():
+    """16^3 coarse blocks with a 2:1 refined octant of 32^3 blocks on [0, 2pi)^3 (both sizes run on
+    the tensor cores): the two-size layout of the 22-field workload, 56 + 8 blocks."""
     nc = 4
     ns, origins, ds, ci, fi = [], [], [], {}, {}
     for bz in range(nc):
@@ -213,7 +213,12 @@ def test_exact_slices_fp32_uneven_blocks(lib, torch):
     for (bz, by, bx), b in fi.items():
         for r, (dz, dy, dxx) in enumerate(W.DIRS):
             nbr[b, r] = fi.get((bz + dz, by + dy, bx + dxx), -1)
-    mesh = W.Mesh(np.asarray(ns), np.asarray(origins), np.repeat(np.asarray(ds)[:, None], 3, 1), nbr, 4)
+    return W.Mesh(np.asarray(ns), np.asarray(origins), np.repeat(np.asarray(ds)[:, None], 3, 1), nbr, 4)
+
+
+def test_exact_slices_fp32_uneven_blocks(lib, torch):
+    """Blocks of 16^3 and 32^3 with analytic ghosts on the level interface, FP32 fields."""
+    mesh = box16_32()
     fields = W.workload_fields(4)[:2]
     per_block = W.sample(mesh, fields, dtype=np.float32)
     buf = W.pack(per_block)
@@ -232,6 +237,67 @@ def test_exact_slices_fp32_uneven_blocks(lib, torch):
             worst = max(worst, err)
     print("fp32 exact-slice max rel err", worst)
     assert worst < TOL_EXACT32
+
+
+def _ghost_slices(dz, dy, dxx, N, g):
+    part = {-1: slice(0, g), 0: slice(g, g + N), 1: slice(g + N, 2 * g + N)}
+    return part[dz], part[dy], part[dxx]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_exchange_analytic_interfaces_then_apply(lib, torch, dtype):
+    """The two-size workload as the benchmark runs it: cfd_exchange_ghosts fills every region
+    that faces a block of the same size (those regions start as NaN on the device), the
+    regions facing the other level hold analytic values (neighbour -1), then all 9 ops on
+    the tensor cores.  Oracle: the same exchange in numpy (Eq. example_G) per size group,
+    then the closed block operators per block."""
+    mesh = box16_32()
+    g, nf = 4, 2
+    fields = W.workload_fields(4)[:nf]
+    per_block = W.sample(mesh, fields, dtype=dtype)
+    dev_blocks = [b.copy() for b in per_block]
+    for b in range(mesh.nblocks):
+        for r, (dz, dy, dxx) in enumerate(W.DIRS):
+            if mesh.neighbors[b, r] >= 0:
+                sz, sy, sx = _ghost_slices(dz, dy, dxx, int(mesh.n[b]), g)
+                dev_blocks[b][:, sz, sy, sx] = np.nan
+    # oracle ghosts: copies of the neighbours' interiors where a neighbour exists
+    ref_blocks = []
+    for q in range(nf):
+        blocks_q = [per_block[b][q].astype(np.float64) for b in range(mesh.nblocks)]
+        for n in np.unique(mesh.n):
+            nbr = mesh.neighbors.copy()
+            nbr[mesh.n != n] = -1
+            blocks_q = C.exchange_ghosts(blocks_q, nbr, int(n), g)
+        ref_blocks.append(blocks_q)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g,
+                            lib.CFD_F32 if dtype == np.float32 else lib.CFD_F64)
+    dev = torch.device("cuda", 0)
+    fields_t = torch.from_numpy(W.pack(dev_blocks)).to(dev)
+    lib.cfd_exchange_ghosts(B, fields_t, nf)
+    nint = sum(int(n) ** 3 for n in mesh.n)
+    out = torch.full((nint * nf * 9,), float("nan"), dtype=fields_t.dtype, device=dev)
+    ws = lib.cfd_apply_workspace(B, nf, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 0)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    lib.cfd_apply(B, fields_t, nf, lib.CFD_OP_ALL, lib.CFD_TC_BF16_EXACT, 0, out, work)
+    lib.cfd_sync_status(B)
+    # the exchange filled exactly the oracle's ghosts
+    ext = W.unpack(fields_t.cpu().numpy(), mesh, nf)
+    for b in range(mesh.nblocks):
+        for q in range(nf):
+            assert np.array_equal(ext[b][q].astype(np.float64), ref_blocks[q][b]), (b, q)
+    got = W.unpack(out.cpu().numpy(), mesh, nf, interior=True, nops=9)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = 0.0
+    for q in range(nf):
+        want = [C.apply_block(ref_blocks[q][b], s1, s2, mesh.dx[b], int(mesh.n[b]), g, OPS) for b in range(mesh.nblocks)]
+        for i, op in enumerate(OPS):
+            wmax = max(np.abs(w[op]).max() for w in want)
+            err = max(np.abs(got[b][q, i].astype(np.float64) - want[b][op]).max() for b in range(mesh.nblocks)) / wmax
+            worst = max(worst, err)
+    print("exchange + analytic interfaces + tensor cores, max rel err", worst)
+    assert worst < (TOL_EXACT32 if dtype == np.float32 else TOL_EXACT64)
 
 
 @pytest.mark.parametrize("n_iter", [0, 1])
