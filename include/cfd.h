@@ -51,10 +51,28 @@ typedef enum cfd_status {
   CFD_ERR_ALLOC = 7           /* host or device allocation failed */
 } cfd_status;
 
-/* Arithmetic of cfd_apply. */
+/*
+ * Arithmetic of cfd_apply.
+ *
+ * The tensor-core forms apply the dense block operator D = A^-1 B ([0]D of
+ * Eq. iter_scheme) per pencil.  Number format of CFD_TC_BF16_EXACT (and of the
+ * hi/lo split, which keeps fewer slices): each pencil (its N + 2 ng ghost-
+ * extended inputs, plus the neighbour values of an iterated pass) is
+ * quantised to 39-bit fixed point relative to its own largest magnitude
+ * (rounded to nearest; a power-of-two scale per pencil), so
+ *   - inputs below 2^-40 of the pencil maximum contribute nothing, and
+ *     subnormal inputs are taken as zero;
+ *   - the error of an output is bounded by ~2^-32 max_j |D_ij| max_j |f_j|
+ *     of its pencil and is typically ~2^-37 sum_j |D_ij f_j|;
+ *   - a NaN or an infinity anywhere in a pencil makes every output of that
+ *     pencil NaN (the FP64 banded solve spreads non-finite values over the
+ *     same pencils);
+ *   - outputs that overflow become infinities; FP64 outputs below the normal
+ *     range flush to zero, FP32 outputs round as IEEE.
+ */
 typedef enum cfd_precision {
   CFD_FP64_BANDED = 0,   /* FP64 right-hand side + Thomas solve per pencil */
-  CFD_TC_BF16X3 = 1,     /* dense D = A^-1 B on BF16 tensor cores, hi/lo split, 3 products */
+  CFD_TC_BF16X3 = 1,     /* dense D on BF16 tensor cores, hi/lo split, 3 products */
   CFD_TC_BF16_EXACT = 2, /* dense D on BF16 tensor cores, exact integer slices (FP64-level result) */
   CFD_TC_TF32 = 3        /* dense D on TF32 tensor cores, one product */
 } cfd_precision;
@@ -176,6 +194,19 @@ cfd_status cfd_apply_workspace(cfd_blocks_t blocks, int nfields, unsigned op_mas
 cfd_status cfd_apply(cfd_blocks_t blocks, const void *fields, int nfields, unsigned op_mask,
                      cfd_precision prec, int n_iter, void *out, void *work, size_t work_bytes,
                      void *stream);
+
+/*
+ * Order of the mixed derivatives on the FP64 banded path.  one_order = 0
+ * (the default) evaluates the symmetrised form of Sec. "Z4c: system
+ * description", (D_i[D_j f] + D_j[D_i f]) / 2; one_order = 1 evaluates
+ * D_i[D_j f] only, half the work.  The two agree to rounding where the block
+ * operators of the two axes commute: every block has same-size face
+ * neighbours along every decomposed axis (closed or iterated systems, cyclic
+ * axes) and its edge ghosts hold the neighbours' values (cfd_exchange_ghosts).
+ * The tensor-core forms always evaluate one order.  Errors: CFD_ERR_ARG,
+ * CFD_ERR_UNSUPPORTED (one order on blocks without face neighbours).
+ */
+cfd_status cfd_blocks_set_mixed_order(cfd_blocks_t blocks, int one_order);
 
 /*
  * Allocation-free variant of cfd_apply for callers that cannot allocate
@@ -439,6 +470,15 @@ const char *cfd_last_error(void);
 unsigned long long cfd_kernel_launches(void);
 cfd_status cfd_profile_enable(int on);
 cfd_status cfd_profile_read(int family, unsigned long long *launches, double *ms);
+
+/*
+ * Test hook (no counterpart in the paper): the number of clock cycles a wait
+ * inside the tensor-core kernel's main loop may take before the kernel gives
+ * up, latches CFD_ERR_TIMEOUT in the handle's status word and ends (after
+ * draining its own copies and MMAs and freeing its tensor memory).
+ * cycles <= 0 restores the default (~2 s).  Process-wide; read at each launch.
+ */
+cfd_status cfd_debug_set_wait_limit(long long cycles);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,7 @@ EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd
            "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_wave_lsrk_workspace", "cfd_wave_lsrk_step",
            "cfd_sync_status", "cfd_last_error",
            "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static",
+           "cfd_debug_set_wait_limit", "cfd_blocks_set_mixed_order",
            "cfd_scheme_set_biased", "cfd_biased_workspace", "cfd_apply_biased", "cfd_advect",
            "cfd_shifted_wave_workspace", "cfd_shifted_wave_lsrk_step", "cfd_advect_lsrk_workspace",
            "cfd_advect_lsrk_step", "cfd_halo_plan_create", "cfd_halo_plan_bytes", "cfd_halo_pack",
@@ -146,6 +147,10 @@ _lib.cfd_profile_enable.argtypes = [c_int]
 _lib.cfd_profile_enable.restype = c_int
 _lib.cfd_profile_read.argtypes = [c_int, POINTER(ctypes.c_ulonglong), POINTER(c_double)]
 _lib.cfd_profile_read.restype = c_int
+_lib.cfd_blocks_set_mixed_order.argtypes = [c_void_p, c_int]
+_lib.cfd_blocks_set_mixed_order.restype = c_int
+_lib.cfd_debug_set_wait_limit.argtypes = [ctypes.c_longlong]
+_lib.cfd_debug_set_wait_limit.restype = c_int
 _lib.cfd_last_error.argtypes = []
 _lib.cfd_last_error.restype = ctypes.c_char_p
 
@@ -436,6 +441,11 @@ def cfd_halo_unpack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
     _check(_lib.cfd_halo_unpack(plan.handle, _ptr(fields), nfields, _ptr(buf), _stream(stream)))
 
 
+def cfd_blocks_set_mixed_order(blocks: Blocks, one_order: bool):
+    """FP64 banded mixed derivatives as D_i D_j only (True) or the symmetrised average (False)."""
+    _check(_lib.cfd_blocks_set_mixed_order(blocks.handle, 1 if one_order else 0))
+
+
 def cfd_sync_status(blocks: Blocks, stream=None):
     """Synchronise the stream and raise a status latched on the device (e.g. a bounded wait that ran out)."""
     _check(_lib.cfd_sync_status(blocks.handle, _stream(stream)))
@@ -470,3 +480,8 @@ def op_mask(ops: Sequence[str]) -> int:
 def ops_in_mask(mask: int):
     """Names of the ops in a bit mask, in output order."""
     return [o for o in OPS if mask & OP_BITS[o]]
+
+
+def cfd_debug_set_wait_limit(cycles: int):
+    """Main-loop wait limit of the tensor-core kernel in clock cycles (<= 0: the default, ~2 s)."""
+    _check(_lib.cfd_debug_set_wait_limit(int(cycles)))

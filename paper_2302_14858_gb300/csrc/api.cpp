@@ -365,7 +365,8 @@ cfd_status apply_banded(cfd_blocks_s *B, const void *fields, int nf, unsigned ma
       } else {
         if (!B->s[0].present) { set_error("mixed ops need the first-degree scheme"); return CFD_ERR_ARG; }
         const int mi = bit - 6;
-        for (int order = 0; order < 2; ++order) {
+        const int norders = B->mixed_one_order ? 1 : 2;  // one order: written directly (out_mode 0)
+        for (int order = 0; order < norders; ++order) {
           const int ai = order == 0 ? kMixed[mi][0] : kMixed[mi][1];  // outer (applied last)
           const int aj = order == 0 ? kMixed[mi][1] : kMixed[mi][0];  // inner
           const int ak = 3 - ai - aj;
@@ -631,6 +632,19 @@ cfd_status cfd_apply(cfd_blocks_t B, const void *fields, int nfields, unsigned o
     return apply_banded(B, fields, nfields, op_mask, n_iter, out, ws, st);
   }
   return dense_apply(B, fields, nfields, op_mask, prec, n_iter, out, work, work_bytes, st);
+}
+
+cfd_status cfd_blocks_set_mixed_order(cfd_blocks_t B, int one_order) {
+  if (!B || (one_order != 0 && one_order != 1)) {
+    set_error("cfd_blocks_set_mixed_order: bad argument");
+    return CFD_ERR_ARG;
+  }
+  if (one_order && !B->iter_ok) {
+    set_error("cfd_blocks_set_mixed_order: one order needs same-size face neighbours on every decomposed axis");
+    return CFD_ERR_UNSUPPORTED;
+  }
+  B->mixed_one_order = one_order != 0;
+  return CFD_OK;
 }
 
 cfd_status cfd_sync_status(cfd_blocks_t B, void *stream) {

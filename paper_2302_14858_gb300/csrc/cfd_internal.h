@@ -147,6 +147,7 @@ struct cfd_blocks_s {
   cfd::BiasedCoef biased;
   std::vector<cfd::BiasedTables> btab; // per distinct N (when biased.present)
   bool iter_ok = true;                 // same-size face neighbours everywhere
+  bool mixed_one_order = false;        // FP64 banded path: d_ij as D_i D_j only (cfd_blocks_set_mixed_order)
   // device copies
   int *d_nbr = nullptr;
   long long *d_extpre = nullptr, *d_intpre = nullptr;

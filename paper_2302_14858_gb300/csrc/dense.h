@@ -51,6 +51,7 @@ struct DenseParams {
   const int *nl;
   CUtensorMap tmap;          // (the type carries its own 128-byte alignment)
   int *status;
+  long long wait_limit;      // clock cycles a main-loop wait may take before it latches CFD_ERR_TIMEOUT
 };
 
 cfd_status dense_bind(cfd_blocks_s *B);

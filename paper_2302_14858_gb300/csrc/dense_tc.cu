@@ -51,6 +51,11 @@ constexpr int kTile = 128;         // pencils per tile (MMA M)
 constexpr int kTmemCols = 512;
 constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (~2 s) before giving up
 
+// ------------------------------------------------------------------ host: wait limit of the main loop
+
+long long g_wait_limit = kWaitLimit;
+long long dense_wait_limit() { return g_wait_limit; }
+
 // ------------------------------------------------------------------ host: operator digits
 
 typedef long double ld;
@@ -319,7 +324,10 @@ __device__ __forceinline__ int tau_exp(int emax, float) { return emax - 126; }
 __device__ __forceinline__ int nonfinite_exp(double) { return 0x7FF; }
 __device__ __forceinline__ int nonfinite_exp(float) { return 0xFF; }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t parity) {
+// Wait for the phase `parity` of an mbarrier for at most `limit` clock cycles.  The main loop
+// uses the launch's limit (DenseParams::wait_limit); the exit path, which drains the CTA's own
+// copies and MMAs before it frees TMEM, always uses kWaitLimit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t parity, long long limit = kWaitLimit) {
   const long long t0 = clock64();
   uint32_t done = 0;
   while (!done) {
@@ -327,7 +335,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_addr, uint32_t p
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(mbar_addr), "r"(parity));
-    if (!done && clock64() - t0 > kWaitLimit) return false;
+    if (!done && clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -542,8 +550,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
   // mbarrier phase are never reused before the epilogue has read them.
   int *s_etau = s_emax + 2 * kParts * kTile;  // [8][128] ring
   uint64_t *bars = reinterpret_cast<uint64_t *>(s_etau + 8 * kTile);
-  // bars: a_empty[2], t_full[3], t_empty[3], meta_full[8], a_full[2], stg_full (thread 0 issues
-  // the MMAs after the a_full wait; the other producers go on to the next tile)
+  // bars: a_empty[2], t_full[3], t_empty[3], meta_full[8], a_full[2], stg_full, drain (thread 0
+  // issues the MMAs after the a_full wait; the other producers go on to the next tile)
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 24);
   const uint32_t bar0 = smem_u32(bars);
   auto a_empty = [&](int i) { return bar0 + 8u * (uint32_t)i; };
@@ -552,6 +560,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
   auto meta_full = [&](int i) { return bar0 + 8u * (uint32_t)(8 + i); };
   auto a_full = [&](int i) { return bar0 + 8u * (uint32_t)(16 + i); };
   const uint32_t stg_full = bar0 + 8u * 18u;
+  const uint32_t drain = bar0 + 8u * 19u;  // the exit path's commit: every MMA this CTA issued has completed
+  const long long WL = P.wait_limit;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = P.N, g = P.g, E = N + 2 * g;
@@ -566,6 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     for (int i = 0; i < kPassBufs; ++i) { mbar_init(t_full(i), 1); mbar_init(t_empty(i), kEpilogue); }
     for (int i = 0; i < 8; ++i) mbar_init(meta_full(i), kProducers);
     mbar_init(stg_full, 1);
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   const int SR = P.seg_rows;
@@ -691,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     };
     const uint32_t lbo = 128, sbo = KP * 16;
     int it = 0, pit = 0;
-    uint32_t last_bar = 0, last_par = 0;  // thread 0: the last MMA commit
+    uint32_t last_bar = 0;  // thread 0: an MMA was issued
     int tile = blockIdx.x;
     if (tile < P.ntiles) {
       if (kind) { if (tid == 0) tma_issue(tile); }
@@ -701,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       const int buf = it & 1, use = it >> 1;
       const TileCoord c = tile_coord(P, tile, pl);
       if (kind) {
-        if (!mbar_wait_bounded(stg_full, (uint32_t)(it & 1))) failed = true;
+        if (!mbar_wait_bounded(stg_full, (uint32_t)(it & 1), WL)) failed = true;
         else if (tid == 0) tma_pending = false;
       } else {
         asm volatile("cp.async.wait_all;");
@@ -733,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         else prefetch(tile + gridDim.x);
       }
       // A[buf] must be free: the MMAs of its previous use have completed
-      if (use > 0 && !mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1))) failed = true;
+      if (use > 0 && !mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1), WL)) failed = true;
       if (half == 0) s_etau[(it & 7) * kTile + pl] = bad_pencil ? kBadTau : tau_exp(emax, TI(0));
       if (bad_pencil) emax = 0;
       uint16_t *Ab = sA + (size_t)buf * (A_BYTES / 2);
@@ -772,12 +783,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       mbar_arrive(a_full(buf));  // A[buf] written by this thread
       if (tid == 0) {
         // MMA issue: once every producer has written A[buf] (the others go on to the next tile)
-        if (!mbar_wait_bounded(a_full(buf), (uint32_t)(use & 1))) failed = true;
+        if (!mbar_wait_bounded(a_full(buf), (uint32_t)(use & 1), WL)) failed = true;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t a0 = smem_u32(sA) + (uint32_t)(buf * A_BYTES);
         for (int ps = 0; ps < P.passes && !failed; ++ps, ++pit) {
           const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
-          if (tuse > 0 && !mbar_wait_bounded(t_empty(tb), (uint32_t)((tuse - 1) & 1))) { failed = true; break; }
+          if (tuse > 0 && !mbar_wait_bounded(t_empty(tb), (uint32_t)((tuse - 1) & 1), WL)) { failed = true; break; }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t b0 = smem_u32(sB) + ps * B_PASS_BYTES;
           const uint32_t cbase = tmem + (uint32_t)(tb * kPassCols);
@@ -802,21 +813,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               t_full(tb)));
+          last_bar = 1;
         }
-        if (!failed) {
+        if (!failed)
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               a_empty(buf)));
-          last_bar = a_empty(buf);
-          last_par = (uint32_t)(use & 1);
-        }
       }
     }
     asm volatile("cp.async.wait_all;");
     if (tid == 0) {
-      // a TMA copy still in flight after a failure completes before the CTA leaves, and the
-      // MMAs issued last complete before TMEM is released
+      // a TMA copy still in flight after a failure completes before the CTA leaves, and every
+      // MMA issued (also those of a tile left half-done by a failed wait) completes before TMEM
+      // is released: one more commit tracks them all
       if (tma_pending) mbar_wait_bounded(stg_full, (uint32_t)(it & 1));
-      if (last_bar) mbar_wait_bounded(last_bar, last_par);
+      if (last_bar) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain));
+        mbar_wait_bounded(drain, 0u);
+      }
     }
   } else {
     // ================================================================ epilogue
@@ -843,13 +856,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     for (int tile = blockIdx.x; tile < P.ntiles && !failed; tile += gridDim.x, ++it) {
       const TileCoord c = tile_coord(P, tile, pl);
       const bool interior = c.valid && P.int_lo1 <= c.t1 && c.t1 < P.int_hi1 && P.int_lo2 <= c.t2 && c.t2 < P.int_hi2;
-      if (!mbar_wait_bounded(meta_full(it & 7), (uint32_t)((it >> 3) & 1))) { failed = true; break; }
+      if (!mbar_wait_bounded(meta_full(it & 7), (uint32_t)((it >> 3) & 1), WL)) { failed = true; break; }
       const int etau = s_etau[(it & 7) * kTile + pl];
       const bool bad = etau == kBadTau;
       const int ebase = etau - 14 - 8 * L;
       for (int ps = 0; ps < P.passes; ++ps, ++pit) {
         const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
-        if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1))) { failed = true; break; }
+        if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1), WL)) { failed = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int RH = R / 2, r0 = ehalf * RH;
         const int sg = r0 / P.seg_rows, i0 = r0 - sg * P.seg_rows;
@@ -934,7 +947,9 @@ cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned g
     if (dev >= 0 && dev < 64) opted[v][dev] = smem;
   }
   launch_begin(KF_DENSE, st);
-  fn<<<grid, kThreads, smem, st>>>(P);
+  DenseParams Q = P;
+  Q.wait_limit = dense_wait_limit();
+  fn<<<grid, kThreads, smem, st>>>(Q);
   launch_end(KF_DENSE, st);
   return cuda_fail(cudaGetLastError(), "k_dense launch");
 }
@@ -1654,3 +1669,11 @@ cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void 
 }
 
 }  // namespace cfd
+
+// Test hook (no counterpart in the paper): the main-loop wait limit of k_dense in clock cycles
+// (<= 0 restores the default of ~2 s).  A tiny limit makes the first waits of a launch run out,
+// so that the timeout path (status word, drained copies and MMAs, freed TMEM) can be checked.
+extern "C" cfd_status cfd_debug_set_wait_limit(long long cycles) {
+  cfd::g_wait_limit = cycles > 0 ? cycles : cfd::kWaitLimit;
+  return CFD_OK;
+}

@@ -170,6 +170,39 @@ def test_uniform_all_ops_fp64(lib, torch, NM, N, n_iter):
             assert err < TOL64, (q, op, err)
 
 
+@pytest.mark.parametrize("n_iter", [0, 1])
+def test_mixed_one_order_equals_symmetrised(lib, torch, n_iter):
+    """cfd_blocks_set_mixed_order(1): d_ij as D_i D_j only matches the oracle's averaged form of
+    Sec. "Z4c: system description" to rounding on a uniform decomposition (the block operators of
+    different axes commute there); single-axis ops are unchanged bit for bit."""
+    NM, N, g = 64, 16, 4
+    fields = case_fields(211, 2)
+    mesh, dx, exts, buf = uniform_case(NM, N, g, fields)
+    s = scheme(lib)
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    both = run_apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, n_iter).reshape(mesh.nblocks, 2, 9, N, N, N)
+    lib.cfd_blocks_set_mixed_order(B, True)
+    one = run_apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, n_iter).reshape(mesh.nblocks, 2, 9, N, N, N)
+    assert np.array_equal(one[:, :, :6], both[:, :, :6])
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    for q in range(2):
+        ref = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, n_iter)
+        for i, op in enumerate(OPS):
+            assert rel_max(one[:, q, i], ref[op].reshape(mesh.nblocks, N, N, N)) < TOL64, op
+    lib.cfd_blocks_set_mixed_order(B, False)
+    again = run_apply(lib, torch, B, buf, 2, lib.CFD_OP_ALL, n_iter).reshape(mesh.nblocks, 2, 9, N, N, N)
+    assert np.array_equal(again, both)
+
+
+def test_mixed_one_order_refused_without_face_neighbours(lib):
+    mesh = mini_box_in_box()
+    s = scheme(lib)
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, mesh.g, lib.CFD_F64)
+    with pytest.raises(lib.CfdError) as e:
+        lib.cfd_blocks_set_mixed_order(B, True)
+    assert e.value.status == lib.CFD_ERR_UNSUPPORTED
+
+
 def test_op_subset_order_and_padé(lib, torch):
     """A subset mask writes only those ops, in bit order; Padé P^1_2 with its closure."""
     NM, N, g = 32, 16, 4
