@@ -24,7 +24,7 @@ struct DenseParams {
   int int_lo1, int_hi1, int_lo2, int_hi2;  // pencils that write final outputs (interior)
   int passes, rows;          // MMA passes per tile, output rows per pass (16 or 32)
   int nseg[2];               // operators (segments of N rows) per pass
-  const uint16_t *seg_img[2][2];
+  const void *seg_img[2][2];  // operator images of the pass's segments (BF16 digits or TF32)
   const int *seg_exp[2][2];
   int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both, 4 halo rows
   int seg_op[2][2];          // op index in the output for final stores

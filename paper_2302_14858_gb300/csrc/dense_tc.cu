@@ -169,6 +169,26 @@ void digit_image(const std::vector<ld> &D, int rows, int cols, int Kp, std::vect
   }
 }
 
+// TF32 image of one operator (the one-product TF32 form): D_ij / 2^rowexp[i] rounded to TF32
+// (nearest, ties to even), canonical K-major smem layout of 32-bit elements:
+// [row/8][k/4][row%8][k%4].  Same row exponents as the digit image.
+void tf32_image(const std::vector<ld> &D, int rows, int cols, int Kp, std::vector<uint32_t> &img) {
+  img.assign((size_t)rows * Kp, 0);
+  for (int i = 0; i < rows; ++i) {
+    ld mx = 0;
+    for (int j = 0; j < cols; ++j) mx = std::max(mx, fabsl(D[(size_t)i * cols + j]));
+    int e = 0;
+    if (mx > 0) frexpl(mx, &e);
+    for (int j = 0; j < cols; ++j) {
+      const float f = (float)ldexpl(D[(size_t)i * cols + j], -e);
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      u = (u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu;
+      img[((size_t)(i / 8) * (Kp / 4) + j / 4) * 32 + (i % 8) * 4 + (j % 4)] = u;
+    }
+  }
+}
+
 // Iterated block system of Eq. iter_center_P in dense form (no dx scaling):
 // unknowns k = -1..N with the derivative fixed at k = -2 (d_lo) and k = N+1
 // (d_hi);  d[k] = sum_j D1[k][j] f_j + cm[k] d_lo + cp[k] d_hi for k = 0..N-1.
@@ -232,6 +252,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
 // BF16 bit pattern (high half of a float) of a small integer, exact for |a| < 2^22.
 __device__ __forceinline__ uint32_t small_int_f32bits(int a) {
   return __float_as_uint(__int_as_float(0x4B400000 + a) - 12582912.0f);
@@ -252,15 +279,40 @@ constexpr int kBadTau = 1 << 20;  // pencil scale of a pencil holding a NaN or a
 // it become infinities, and `bad` gives a NaN; without it the caller has established that
 // the exponent stays in range for every Y.
 template <bool checked>
-__device__ __forceinline__ double scaled_int_to_double(long long Y, int E, bool bad) {
-  const double d = __ll2double_rn(Y);
+__device__ __forceinline__ double scaled_double(double d, int E, bool bad) {
   const int hi = __double2hiint(d), lo = __double2loint(d);
-  if (!checked) return Y == 0 ? 0.0 : __hiloint2double(hi + (E << 20), lo);
-  const int fe = (hi >> 20) & 0x7FF;  // 0 only for Y = 0
+  if (!checked) return d == 0.0 ? 0.0 : __hiloint2double(hi + (E << 20), lo);
+  const int fe = (hi >> 20) & 0x7FF;  // 0 only for d = 0 here (d is an integer or an FP32 value)
   if (bad) return __longlong_as_double(0x7FF8000000000000ll);
   if (fe == 0 || fe + E <= 0) return __hiloint2double(hi & (int)0x80000000, 0);
   if (fe + E >= 2047) return __hiloint2double((hi & (int)0x80000000) | 0x7FF00000, 0);
   return __hiloint2double(hi + (E << 20), lo);
+}
+template <bool checked>
+__device__ __forceinline__ double scaled_int_to_double(long long Y, int E, bool bad) {
+  return scaled_double<checked>(__ll2double_rn(Y), E, bad);
+}
+
+// v / tau as TF32 (rounded to nearest, ties away from zero), tau = 2^(emax - bias + 1) the
+// pencil's power-of-two scale: an add to the exponent field keeps every element a normal number
+// (elements more than 2^-60 below the pencil maximum, and subnormals, are zero), then one
+// rounding to FP32 and one to TF32.
+__device__ __forceinline__ uint32_t cvt_rna_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ uint32_t tf32_of(double v, int emax) {
+  const int hi = __double2hiint(v), lo = __double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  if (e == 0 || e + 60 < emax) return 0u;
+  return cvt_rna_tf32(__double2float_rn(__hiloint2double(hi - ((emax - 1022) << 20), lo)));
+}
+__device__ __forceinline__ uint32_t tf32_of(float v, int emax) {
+  const uint32_t u = __float_as_uint(v);
+  const int e = (int)((u >> 23) & 0xFF);
+  if (e == 0 || e + 60 < emax) return 0u;
+  return cvt_rna_tf32(__uint_as_float(u - ((uint32_t)(emax - 126) << 23)));
 }
 
 // y * 2^E in FP32 for |E| <= 300: two exact power-of-two factors (each a normal float),
@@ -384,7 +436,7 @@ constexpr int kBiasBytes = (kTile + kBiasRows) * 16 * 2;
 // (TMEM lane) from the pass buffer, release it (the last group), rebuild every output as
 // Y * 2^(rowexp + ebase) and store it.  `checked` selects the conversion that handles
 // non-finite pencils and exponents outside the normal range (see scaled_int_to_double).
-template <int RH, int LEV, typename TO, bool checked>
+template <int RH, int LEV, typename TO, bool checked, int TFM>
 __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int ebase, bool bad,
                                               const int *rowexp, TO *fin_base, long long fin_stride, double *sc_base,
                                               long long sc_stride, bool write_fin, bool write_sc, int i0,
@@ -441,7 +493,17 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
       };
       TO val;
       double dv = 0.0;  // the FP64 value the intermediates and halo values keep
-      if constexpr (sizeof(TO) == 8) {
+      if constexpr (TFM) {
+        // TF32 form: one FP32 accumulator per output, scaled by 2^(rowexp + etau)
+        const float a = __uint_as_float(acc[0][c]);
+        if constexpr (sizeof(TO) == 8) {
+          val = dv = scaled_double<checked>((double)a, ex, bad);
+        } else {
+          if constexpr (checked) val = bad ? __int_as_float(0x7FC00000) : scale_pow2(a, ex);
+          else val = a * __int_as_float((ex + 127) << 23);
+          if (write_sc) dv = scaled_double<true>((double)a, ex, bad);
+        }
+      } else if constexpr (sizeof(TO) == 8) {
         val = dv = scaled_int_to_double<checked>(exact_y(), ex, bad);
       } else {
         // FP32 outputs: the levels as exact floats, Horner in FP32 (each rounding is relative to
@@ -518,10 +580,13 @@ __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, 
   return c;
 }
 
-template <typename TI, typename TO, int KP, int S, int L>
+// TFM = 1: the one-product TF32 form (S = 1, L = 0): A = the pencils scaled by tau and rounded
+// to TF32, B = the TF32 image of D, one kind::tf32 MMA chain per pass, FP32 accumulators.
+template <typename TI, typename TO, int KP, int S, int L, int TFM>
 __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr int A_BYTES = S * kTile * KP * 2;
+  constexpr int EB = TFM ? 4 : 2;  // bytes per operand element (TF32 or BF16)
+  constexpr int A_BYTES = S * kTile * KP * EB;
   // cp.async staging row pitch (elements): odd for the y/z axes (one element per thread and
   // copy, spread over the banks); for the x axis, where a pencil is a contiguous row copied in
   // 16-byte chunks, a pitch whose rows stay 16-byte aligned.
@@ -531,10 +596,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
   const int pitch = xrow ? KP + VE : KP + 1;
   constexpr int NCH = KP / 8;    // 8-value K chunks per pencil
   const int R = P.rows;
-  const int B_PASS_BYTES = S * R * KP * 2;
+  const int B_PASS_BYTES = S * R * KP * EB;
   const int kind = P.tma_kind;
-  uint16_t *sA = reinterpret_cast<uint16_t *>(smem);  // [2][S][128][KP]
-  uint16_t *sB = reinterpret_cast<uint16_t *>(smem + 2 * A_BYTES);
+  uint16_t *sA = reinterpret_cast<uint16_t *>(smem);  // [2][S][128][KP] (32-bit elements for TF32)
+  unsigned char *sB = smem + 2 * A_BYTES;
   // operands of the bias MMA (K = 16, canonical K-major): A = 1 in column 0 of all 128 rows,
   // B = kAccBias in column 0 of the (L + 1) R level rows
   uint16_t *sOne = reinterpret_cast<uint16_t *>(smem + 2 * A_BYTES + 2 * B_PASS_BYTES);
@@ -583,10 +648,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
   for (int ps = 0; ps < P.passes; ++ps) {
     for (int sg = 0; sg < P.nseg[ps]; ++sg) {
       const uint4 *src = reinterpret_cast<const uint4 *>(P.seg_img[ps][sg]);
-      const int slice_u4 = SR * KP * 2 / 16;
+      const int slice_u4 = SR * KP * EB / 16;
       for (int t = 0; t < S; ++t) {
-        uint4 *dst = reinterpret_cast<uint4 *>(sB + (size_t)ps * (B_PASS_BYTES / 2) + (size_t)t * R * KP +
-                                               (size_t)sg * SR * KP);
+        uint4 *dst = reinterpret_cast<uint4 *>(sB + (size_t)ps * B_PASS_BYTES + ((size_t)t * R * KP +
+                                               (size_t)sg * SR * KP) * EB);
         const uint4 *sp = src + (size_t)t * slice_u4;
         for (int i = tid; i < slice_u4; i += kThreads) dst[i] = __ldg(sp + i);
       }
@@ -749,6 +814,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       if (bad_pencil) emax = 0;
       uint16_t *Ab = sA + (size_t)buf * (A_BYTES / 2);
       const int row_group = pl >> 3, row_in = pl & 7;
+      if constexpr (TFM) {
+        // TF32 rows: chunk ch (8 values) fills core-matrix columns 2 ch and 2 ch + 1
+        uint32_t *A32 = reinterpret_cast<uint32_t *>(Ab);
+#pragma unroll
+        for (int h = 0; h < CPP; ++h) {
+          const int ch = half + kParts * h;
+          if (ch >= NCH) break;
+          uint32_t w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) w[k] = (emax && ch * 8 < P.kext) ? tf32_of(v[h][k], emax) : 0u;
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            *reinterpret_cast<uint4 *>(A32 + ((size_t)row_group * (KP / 4) + 2 * ch + q) * 32 + row_in * 4) =
+                make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+      } else {
 #pragma unroll
       for (int h = 0; h < CPP; ++h) {
         const int ch = half + kParts * h;
@@ -778,6 +859,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
           *dst = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
         }
       }
+      }
       asm volatile("fence.proxy.async.shared::cta;");
       mbar_arrive(meta_full(it & 7));
       mbar_arrive(a_full(buf));  // A[buf] written by this thread
@@ -792,6 +874,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t b0 = smem_u32(sB) + ps * B_PASS_BYTES;
           const uint32_t cbase = tmem + (uint32_t)(tb * kPassCols);
+          if constexpr (TFM) {
+            // one product: K steps of 8 TF32 values (32 bytes = two core matrices)
+            const uint32_t idesc_t = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(R >> 3) << 17) |
+                                     ((uint32_t)(kTile >> 4) << 24);
+#pragma unroll
+            for (int kk = 0; kk < KP / 8; ++kk)
+              mma_tf32(cbase, smem_desc(a0 + (uint32_t)(kk * 256), 128, KP * 32),
+                       smem_desc(b0 + (uint32_t)(kk * 256), 128, KP * 32), idesc_t, kk ? 1u : 0u);
+          } else {
           {
             // every level column of the pass buffer starts at kAccBias (1 x kAccBias, K = 16)
             const uint32_t idesc_b = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(((L + 1) * R) >> 3) << 17) |
@@ -810,6 +901,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
               const uint64_t db = smem_desc(b0 + (uint32_t)(kk * 256), lbo, sbo);
               mma_bf16(cbase + (uint32_t)(s * R), da, db, idesc_s, 1u);
             }
+          }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               t_full(tb)));
@@ -851,7 +943,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       rlo1 = min(rlo1, s_rowexp[48 + i]);
       rhi1 = max(rhi1, s_rowexp[48 + i]);
     }
-    constexpr int kExLo = sizeof(TO) == 8 ? -1022 : -126, kExHi = sizeof(TO) == 8 ? 969 : 127;
+    // unchecked conversion: Y * 2^E (|Y| < 2^55) or a * 2^E (an FP32 accumulator) stays normal
+    constexpr int kExLo = sizeof(TO) == 8 ? (TFM ? -870 : -1022) : -126;
+    constexpr int kExHi = sizeof(TO) == 8 ? (TFM ? 1000 : 969) : 127;
     int it = 0, pit = 0;
     for (int tile = blockIdx.x; tile < P.ntiles && !failed; tile += gridDim.x, ++it) {
       const TileCoord c = tile_coord(P, tile, pl);
@@ -859,7 +953,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       if (!mbar_wait_bounded(meta_full(it & 7), (uint32_t)((it >> 3) & 1), WL)) { failed = true; break; }
       const int etau = s_etau[(it & 7) * kTile + pl];
       const bool bad = etau == kBadTau;
-      const int ebase = etau - 14 - 8 * L;
+      const int ebase = TFM ? etau : etau - 14 - 8 * L;
       for (int ps = 0; ps < P.passes; ++ps, ++pit) {
         const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
         if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1), WL)) { failed = true; break; }
@@ -905,15 +999,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const bool safe = !(wf || ws) || (!bad && ebase + rlo >= kExLo && ebase + rhi <= kExHi);
         if (__all_sync(0xffffffffu, safe)) {
           if (RH == 16)
-            epilogue_rows<8, L + 1, TO, false>(taddr, (uint32_t)R, ebase, bad, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u,
+            epilogue_rows<8, L + 1, TO, false, TFM>(taddr, (uint32_t)R, ebase, bad, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u,
                                                srows, P.xvec != 0, gx, gyp);
-          epilogue_rows<8, L + 1, TO, false>(taddr + (RH - 8), (uint32_t)R, ebase, bad, rexp + (RH - 8), fb, f_ax, sb,
+          epilogue_rows<8, L + 1, TO, false, TFM>(taddr + (RH - 8), (uint32_t)R, ebase, bad, rexp + (RH - 8), fb, f_ax, sb,
                                              sstr, wf, ws, i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0, gx, gyp);
         } else {
           if (RH == 16)
-            epilogue_rows<8, L + 1, TO, true>(taddr, (uint32_t)R, ebase, bad, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u,
+            epilogue_rows<8, L + 1, TO, true, TFM>(taddr, (uint32_t)R, ebase, bad, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u,
                                               srows, P.xvec != 0, gx, gyp);
-          epilogue_rows<8, L + 1, TO, true>(taddr + (RH - 8), (uint32_t)R, ebase, bad, rexp + (RH - 8), fb, f_ax, sb,
+          epilogue_rows<8, L + 1, TO, true, TFM>(taddr + (RH - 8), (uint32_t)R, ebase, bad, rexp + (RH - 8), fb, f_ax, sb,
                                             sstr, wf, ws, i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0, gx, gyp);
         }
       }
@@ -929,14 +1023,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
 template <typename TI, typename TO, int KP>
 cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned grid, cudaStream_t st) {
   void (*fn)(const __grid_constant__ DenseParams);
-  if (S == 5 && L == 4) fn = k_dense<TI, TO, KP, 5, 4>;
-  else if (S == 2 && L == 1) fn = k_dense<TI, TO, KP, 2, 1>;
+  if (S == 5 && L == 4) fn = k_dense<TI, TO, KP, 5, 4, 0>;
+  else if (S == 2 && L == 1) fn = k_dense<TI, TO, KP, 2, 1, 0>;
+  else if (S == 1 && L == 0) fn = k_dense<TI, TO, KP, 1, 0, 1>;
   else { set_error("dense: unsupported slice configuration"); return CFD_ERR_UNSUPPORTED; }
   // The shared-memory opt-in is set once per device and instantiation (and raised when a
   // launch needs more), so that later calls issue nothing but the launch: a stream being
   // captured into a CUDA graph sees only kernel nodes.
-  static size_t opted[2][64] = {};  // [slice configuration][device]
-  const int v = S == 5 ? 0 : 1;
+  static size_t opted[3][64] = {};  // [slice configuration][device]
+  const int v = S == 5 ? 0 : (S == 2 ? 1 : 2);
   int dev = 0;
   cfd_status s = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
   if (s != CFD_OK) return s;
@@ -966,8 +1061,10 @@ cfd_status launch_types(const DenseParams &P, int KP, int S, int L, size_t smem,
 // ------------------------------------------------------------------ host planning
 
 struct DenseOp {        // one (group, axis, degree) operator
-  uint16_t *img = nullptr;  // device: kS x N x Kp digits
-  int *rowexp = nullptr;    // device: N
+  uint16_t *img = nullptr;    // device: kS x N x Kp digits
+  uint32_t *img32 = nullptr;  // device: N x Kp TF32 values (the one-product TF32 form)
+  int *rowexp = nullptr;      // device: N
+  const void *image(bool tf32) const { return tf32 ? (const void *)img32 : (const void *)img; }
 };
 
 struct DenseGroup {
@@ -998,10 +1095,16 @@ DenseState *state_of(cfd_blocks_s *B) { return reinterpret_cast<DenseState *>(B-
 
 static cfd_status upload_op(cfd_blocks_s *B, const std::vector<ld> &D, int rows, int cols, int Kp, DenseOp &o) {
   std::vector<uint16_t> img;
+  std::vector<uint32_t> img32;
   std::vector<int> rexp;
   digit_image(D, rows, cols, Kp, img, rexp);
+  tf32_image(D, rows, cols, Kp, img32);
   cfd_status s = cuda_fail(cudaMalloc((void **)&o.img, img.size() * 2), "cudaMalloc");
   if (s == CFD_OK) s = cuda_fail(cudaMemcpy(o.img, img.data(), img.size() * 2, cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (s == CFD_OK) s = cuda_fail(cudaMalloc((void **)&o.img32, img32.size() * 4), "cudaMalloc");
+  if (s == CFD_OK)
+    s = cuda_fail(cudaMemcpy(o.img32, img32.data(), img32.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (o.img32) B->d_dense_ptrs.push_back(o.img32);
   if (s == CFD_OK) s = cuda_fail(cudaMalloc((void **)&o.rowexp, rexp.size() * 4), "cudaMalloc");
   if (s == CFD_OK) s = cuda_fail(cudaMemcpy(o.rowexp, rexp.data(), rexp.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
   if (o.img) B->d_dense_ptrs.push_back(o.img);
@@ -1162,14 +1265,16 @@ namespace {
 // 0..4 (15 slice pairs), for FP32 fields too -- four slices and levels 0..3 measured ~1e-6 on
 // second derivatives at fine spacing (the truncated fifth operator digit acts coherently on
 // smooth data), ten times the FP32 rounding of the outputs.
-int slices_of(cfd_precision p, int) { return p == CFD_TC_BF16_EXACT ? 5 : 2; }
-int levels_of(cfd_precision p, int) { return p == CFD_TC_BF16_EXACT ? 4 : 1; }
+int slices_of(cfd_precision p, int) { return p == CFD_TC_BF16_EXACT ? 5 : (p == CFD_TC_TF32 ? 1 : 2); }
+int levels_of(cfd_precision p, int) { return p == CFD_TC_BF16_EXACT ? 4 : (p == CFD_TC_TF32 ? 0 : 1); }
+bool tc_precision(cfd_precision p) { return p == CFD_TC_BF16_EXACT || p == CFD_TC_BF16X3 || p == CFD_TC_TF32; }
 
 // Shared memory per CTA: two A digit buffers, B digits of two passes, the
 // input staging tile, row exponents, exponent exchange, etau ring, barriers.  At least 116 KB so that
 // one CTA (holding all 512 TMEM columns) occupies an SM.
 size_t dense_smem(int KP, int S, int rows, size_t elem, int tma_boxes) {
-  const size_t ab = 2 * (size_t)S * kTile * KP * 2 + 2 * (size_t)S * rows * KP * 2;
+  const size_t eb = S == 1 ? 4 : 2;  // TF32 or BF16 operands
+  const size_t ab = 2 * (size_t)S * kTile * KP * eb + 2 * (size_t)S * rows * KP * eb;
   const size_t stg = std::max((size_t)kTile * (KP + 16 / elem) * elem, (size_t)tma_boxes * kTile * 128);
   const size_t need = ((ab + kBiasBytes + 1023) & ~(size_t)1023) + stg + (2 * 48 + 2 * kParts * kTile + 8 * kTile) * 4 +
                       24 * 8 + 64;
@@ -1266,9 +1371,9 @@ static DensePlanSizes dense_sizes(const cfd_blocks_s *B, int nf, unsigned mask, 
 }
 
 cfd_status dense_workspace(cfd_blocks_s *B, int nf, unsigned mask, cfd_precision prec, int n_iter, size_t *bytes) {
-  if (prec != CFD_TC_BF16_EXACT && prec != CFD_TC_BF16X3) {
-    set_error("tensor-core precision not available (TF32 is not built)");
-    return CFD_ERR_UNSUPPORTED;
+  if (!tc_precision(prec)) {
+    set_error("unknown precision");
+    return CFD_ERR_ARG;
   }
   const DensePlanSizes z = dense_sizes(B, nf, mask, n_iter);
   *bytes = bytes256(z.gy) + bytes256(z.gz) + 2 * bytes256(z.halo) + 256;
@@ -1375,7 +1480,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         for (int k = 0; k < per_pass; ++k) {
           const int sgi = ps * per_pass + k;
           const DenseOp &o = iterating(box) ? G.opI[box][deg[sgi] - 1] : G.op[box][deg[sgi] - 1];
-          P.seg_img[ps][k] = o.img;
+          P.seg_img[ps][k] = o.image(prec == CFD_TC_TF32);
           P.seg_exp[ps][k] = o.rowexp;
           P.seg_mode[ps][k] = mode[sgi];
           P.seg_op[ps][k] = op[sgi];
@@ -1402,7 +1507,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       H.scratch_out = nullptr;
       for (int it = 0; it < n_iter; ++it) {
         const DenseOp &o = it == 0 ? G.halo0[box] : G.haloI[box];
-        H.seg_img[0][0] = o.img;
+        H.seg_img[0][0] = o.image(prec == CFD_TC_TF32);
         H.seg_exp[0][0] = o.rowexp;
         H.halo_in = it == 0 ? nullptr : halo[(it - 1) & 1];
         H.halo_out = halo[it & 1];
@@ -1535,9 +1640,9 @@ size_t dense_biased_workspace(const cfd_blocks_s *B, int nf, int n_iter, bool ad
 cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void *beta, const int *axes, int naxes,
                         int mode, cfd_precision prec, int n_iter, void *out, int out_nops, int out_opidx,
                         bool accum_all, void *work, size_t work_bytes, cudaStream_t st) {
-  if (prec != CFD_TC_BF16_EXACT && prec != CFD_TC_BF16X3) {
-    set_error("tensor-core precision not available (TF32 is not built)");
-    return CFD_ERR_UNSUPPORTED;
+  if (!tc_precision(prec)) {
+    set_error("unknown precision");
+    return CFD_ERR_ARG;
   }
   DenseState *ds = state_of(B);
   if (!ds) { set_error("dense: operators were not built at bind"); return CFD_ERR_UNSUPPORTED; }
@@ -1634,7 +1739,7 @@ cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void 
         for (int k = 0; k < per_pass; ++k) {
           const int sgi = ps * per_pass + k;
           const DenseOp &o = iter ? G.bopI[box][side[sgi]] : G.bop[box][side[sgi]];
-          P.seg_img[ps][k] = o.img;
+          P.seg_img[ps][k] = o.image(prec == CFD_TC_TF32);
           P.seg_exp[ps][k] = o.rowexp;
           P.seg_mode[ps][k] = 0;
           P.seg_op[ps][k] = op[sgi];
@@ -1651,7 +1756,7 @@ cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void 
         H.seg_op[0][0] = 0;
         for (int it = 0; it < n_iter; ++it) {
           const DenseOp &o = it == 0 ? G.bhalo0[box] : G.bhaloI[box];
-          H.seg_img[0][0] = o.img;
+          H.seg_img[0][0] = o.image(prec == CFD_TC_TF32);
           H.seg_exp[0][0] = o.rowexp;
           H.halo_in = it == 0 ? nullptr : halo[(it - 1) & 1];
           H.halo_out = halo[it & 1];

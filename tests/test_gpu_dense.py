@@ -185,6 +185,45 @@ def test_exact_slices_single_periodic_block(lib, torch):
     assert rel_max(got[1], np.moveaxis(want_dyy, 0, 1)) < TOL_EXACT64
 
 
+# Measured bounds of the one-product TF32 form (max relative error per op against the oracle,
+# seeded sine/Gaussian fields), asserted with a factor ~2 of slack: (first-degree, second-degree,
+# mixed).  Measured on GB300: 64^3 8.2e-3 / 9.3e-2 / 1.05e-1 (16^3 blocks), 7.6e-3 / 9.4e-2 /
+# 1.03e-1 (32^3 blocks); 128^3 1.9e-2 / 3.7e-1 / 4.9e-1.  RMS errors are ~30x smaller.
+TF32_BOUNDS = {(64, 16): (1.6e-2, 1.9e-1, 2.1e-1), (64, 32): (1.6e-2, 1.9e-1, 2.1e-1), (128, 32): (4e-2, 7.5e-1, 1.0)}
+
+
+@pytest.mark.parametrize("NM,N", [(64, 16), (64, 32), (128, 32)])
+def test_tf32_one_product_measured_bound(lib, torch, NM, N):
+    """CFD_TC_TF32: one TF32 product with FP32 accumulation.  Its error is the TF32 rounding of
+    the pencil (relative to its scale) and of D, ~2^-11 of sum_j |D_ij f_j|, times the
+    cancellation sum_j |D_ij f_j| / |D f| that grows like dx^-d: a usable bound for first
+    derivatives on coarse grids only.  The max and RMS relative error per op are printed and
+    the measured bound is asserted per degree."""
+    g = 4
+    fs = fields4(700 + NM + N)
+    mesh, dx, exts, buf = uniform(NM, N, g, fs)
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    nf = len(fs)
+    got = apply(lib, torch, B, buf, nf, lib.CFD_OP_ALL, lib.CFD_TC_TF32).reshape(mesh.nblocks, nf, 9, N, N, N)
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    worst = {op: 0.0 for op in OPS}
+    rms = {op: 0.0 for op in OPS}
+    for q in range(nf):
+        ref = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, 0)
+        for i, op in enumerate(OPS):
+            want = ref[op].reshape(mesh.nblocks, N, N, N)
+            den = np.abs(want).max()
+            worst[op] = max(worst[op], rel_max(got[:, q, i], want))
+            rms[op] = max(rms[op], float(np.sqrt(np.mean((got[:, q, i] - want) ** 2))) / den)
+    print(f"TF32 {NM}^3/{N}^3 max rel err", {k: f"{v:.2e}" for k, v in worst.items()})
+    print(f"TF32 {NM}^3/{N}^3 rms rel err", {k: f"{v:.2e}" for k, v in rms.items()})
+    b1, b2, bm = TF32_BOUNDS[(NM, N)]
+    for op in OPS:
+        bound = b2 if op in ("dxx", "dyy", "dzz") else (bm if op in ("dxy", "dxz", "dyz") else b1)
+        assert worst[op] < bound, (op, worst[op])
+
+
 def box16_32():
     """16^3 coarse blocks with a 2:1 refined octant of 32^3 blocks on [0, 2pi)^3 (both sizes run on
     the tensor cores): the two-size layout of the 22-field workload, 56 + 8 blocks."""
