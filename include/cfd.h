@@ -201,6 +201,24 @@ cfd_status cfd_apply(cfd_blocks_t blocks, const void *fields, int nfields, unsig
                      void *stream);
 
 /*
+ * Autotuner of the tensor-core form (no counterpart in the paper): runs the request
+ * cfd_apply(blocks, fields, nfields, op_mask, prec, n_iter, out, work, ...) once, launching
+ * each of its kernels under every candidate launch configuration -- the staging of the input
+ * tiles (TMA boxes or cp.async) and the order in which the persistent CTAs take the tiles
+ * (interleaved or contiguous runs) -- three times, timing the last two with CUDA events, and
+ * keeps the fastest per kernel of the request in the handle; later cfd_apply calls of the same
+ * request (fields, ops, precision, iterations) use those choices.  Synchronises the stream (not
+ * for use during stream capture); `out` receives the request's results.  Errors: as cfd_apply,
+ * CFD_ERR_ARG for the FP64 banded path (nothing to tune).
+ */
+cfd_status cfd_autotune(cfd_blocks_t blocks, const void *fields, int nfields, unsigned op_mask, cfd_precision prec,
+                        int n_iter, void *out, void *work, size_t work_bytes, void *stream);
+
+/* The autotuner's choices and measured times as a JSON object (request -> per-kernel list),
+ * written to buf (len bytes, NUL-terminated, truncated if short); *needed = bytes required. */
+cfd_status cfd_autotune_report(cfd_blocks_t blocks, char *buf, size_t len, size_t *needed);
+
+/*
  * Order of the mixed derivatives on the FP64 banded path.  one_order = 0
  * (the default) evaluates the symmetrised form of Sec. "Z4c: system
  * description", (D_i[D_j f] + D_j[D_i f]) / 2; one_order = 1 evaluates

@@ -43,7 +43,7 @@ EXPORTS = ("cfd_scheme_create", "cfd_scheme_closure", "cfd_scheme_destroy", "cfd
            "cfd_wave_workspace", "cfd_wave_rk_step", "cfd_wave_lsrk_workspace", "cfd_wave_lsrk_step",
            "cfd_sync_status", "cfd_last_error",
            "cfd_kernel_launches", "cfd_profile_enable", "cfd_profile_read", "cfd_apply_static",
-           "cfd_debug_set_wait_limit", "cfd_blocks_set_mixed_order",
+           "cfd_debug_set_wait_limit", "cfd_blocks_set_mixed_order", "cfd_autotune", "cfd_autotune_report",
            "cfd_scheme_set_biased", "cfd_biased_workspace", "cfd_apply_biased", "cfd_advect",
            "cfd_shifted_wave_workspace", "cfd_shifted_wave_lsrk_step", "cfd_advect_lsrk_workspace",
            "cfd_advect_lsrk_step", "cfd_halo_plan_create", "cfd_halo_plan_bytes", "cfd_halo_pack",
@@ -147,6 +147,11 @@ _lib.cfd_profile_enable.argtypes = [c_int]
 _lib.cfd_profile_enable.restype = c_int
 _lib.cfd_profile_read.argtypes = [c_int, POINTER(ctypes.c_ulonglong), POINTER(c_double)]
 _lib.cfd_profile_read.restype = c_int
+_lib.cfd_autotune.argtypes = [c_void_p, c_void_p, c_int, ctypes.c_uint, c_int, c_int, c_void_p, c_void_p, ctypes.c_size_t,
+                              c_void_p]
+_lib.cfd_autotune.restype = c_int
+_lib.cfd_autotune_report.argtypes = [c_void_p, ctypes.c_char_p, ctypes.c_size_t, POINTER(ctypes.c_size_t)]
+_lib.cfd_autotune_report.restype = c_int
 _lib.cfd_blocks_set_mixed_order.argtypes = [c_void_p, c_int]
 _lib.cfd_blocks_set_mixed_order.restype = c_int
 _lib.cfd_debug_set_wait_limit.argtypes = [ctypes.c_longlong]
@@ -439,6 +444,24 @@ def cfd_halo_pack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
 def cfd_halo_unpack(plan: HaloPlan, fields, nfields: int, buf, stream=None):
     """Write `buf` (plan order) into the plan's ghost regions of every field."""
     _check(_lib.cfd_halo_unpack(plan.handle, _ptr(fields), nfields, _ptr(buf), _stream(stream)))
+
+
+def cfd_autotune(blocks: Blocks, fields, nfields: int, op_mask: int, prec: int, n_iter: int, out, work,
+                 stream=None, work_bytes=None):
+    """cfd_apply once with every kernel launched under each candidate configuration; the fastest
+    per kernel is kept for later calls of the same request (synchronises the stream)."""
+    _check(_lib.cfd_autotune(blocks.handle, _ptr(fields), nfields, op_mask, prec, n_iter, _ptr(out), _ptr(work),
+                             _nbytes(work, work_bytes), _stream(stream)))
+
+
+def cfd_autotune_report(blocks: Blocks) -> dict:
+    """The autotuner's choices and times: {request: [{stage, staging, order, ms}, ...]}."""
+    import json
+    need = ctypes.c_size_t(0)
+    _check(_lib.cfd_autotune_report(blocks.handle, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(_lib.cfd_autotune_report(blocks.handle, buf, need.value, ctypes.byref(need)))
+    return json.loads(buf.value.decode())
 
 
 def cfd_blocks_set_mixed_order(blocks: Blocks, one_order: bool):

@@ -634,6 +634,30 @@ cfd_status cfd_apply(cfd_blocks_t B, const void *fields, int nfields, unsigned o
   return dense_apply(B, fields, nfields, op_mask, prec, n_iter, out, work, work_bytes, st);
 }
 
+cfd_status cfd_autotune(cfd_blocks_t B, const void *fields, int nfields, unsigned op_mask, cfd_precision prec,
+                        int n_iter, void *out, void *work, size_t work_bytes, void *stream) {
+  if (!B || prec == CFD_FP64_BANDED) {
+    set_error("cfd_autotune: a blocks handle and a tensor-core precision are needed");
+    return CFD_ERR_ARG;
+  }
+  dense_set_tuning(B, true);
+  const cfd_status s = cfd_apply(B, fields, nfields, op_mask, prec, n_iter, out, work, work_bytes, stream);
+  dense_set_tuning(B, false);
+  return s;
+}
+
+cfd_status cfd_autotune_report(cfd_blocks_t B, char *buf, size_t len, size_t *needed) {
+  if (!B || (!buf && len) || !needed) { set_error("cfd_autotune_report: bad argument"); return CFD_ERR_ARG; }
+  const std::string r = dense_tuning_report(B);
+  *needed = r.size() + 1;
+  if (buf && len) {
+    const size_t n = std::min(len - 1, r.size());
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
+  }
+  return CFD_OK;
+}
+
 cfd_status cfd_blocks_set_mixed_order(cfd_blocks_t B, int one_order) {
   if (!B || (one_order != 0 && one_order != 1)) {
     set_error("cfd_blocks_set_mixed_order: bad argument");

@@ -29,6 +29,7 @@ struct DenseParams {
   int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both, 4 halo rows
   int seg_op[2][2];          // op index in the output for final stores
   int tiles_per_job, ntiles; // 128-pencil tiles per (block, field); all tiles of the stage
+  int tile_order, tiles_per_cta;  // 0: tile = CTA + k grid; 1: contiguous runs of tiles_per_cta
   int seg_rows;              // operator rows per segment (N, or 16 for a halo pass)
   int kext;                  // K values loaded per pencil: N + 2g, or N + 2g + 4 with halo columns
   const double *halo_in;     // [nblocks][nf][n1 n2][4]: previous iterate at rows 1, N-2 per degree (x dx^d)
@@ -55,6 +56,8 @@ struct DenseParams {
 };
 
 cfd_status dense_bind(cfd_blocks_s *B);
+void dense_set_tuning(cfd_blocks_s *B, bool on);
+std::string dense_tuning_report(cfd_blocks_s *B);
 cfd_status dense_workspace(cfd_blocks_s *B, int nf, unsigned mask, cfd_precision prec, int n_iter, size_t *bytes);
 cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mask, cfd_precision prec, int n_iter,
                        void *out, void *work, size_t work_bytes, cudaStream_t st);

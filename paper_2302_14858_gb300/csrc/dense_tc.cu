@@ -34,10 +34,13 @@
 //   5. all threads wait (bounded), read their TMEM lane (= pencil) with
 //      tcgen05.ld, rebuild each output and store it.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "dense.h"
@@ -556,6 +559,25 @@ struct TileCoord {
   bool valid;
 };
 
+// The tiles of this CTA: interleaved (tile = CTA + k * grid) or a contiguous run of
+// tiles_per_cta (tile_order 1; neighbouring tiles share input rows in L2).
+struct TileRange {
+  int first, end, step;
+};
+__device__ __forceinline__ TileRange tile_range(const DenseParams &P) {
+  TileRange r;
+  if (P.tile_order) {
+    r.first = blockIdx.x * P.tiles_per_cta;
+    r.end = min(P.ntiles, r.first + P.tiles_per_cta);
+    r.step = 1;
+  } else {
+    r.first = blockIdx.x;
+    r.end = P.ntiles;
+    r.step = gridDim.x;
+  }
+  return r;
+}
+
 __device__ __forceinline__ int dir_index_dev(int dz, int dy, int dx) {
   const int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
   return r > 13 ? r - 1 : r;
@@ -768,12 +790,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     const uint32_t lbo = 128, sbo = KP * 16;
     int it = 0, pit = 0;
     uint32_t last_bar = 0;  // thread 0: an MMA was issued
-    int tile = blockIdx.x;
-    if (tile < P.ntiles) {
+    const TileRange tr = tile_range(P);
+    int tile = tr.first;
+    if (tile < tr.end) {
       if (kind) { if (tid == 0) tma_issue(tile); }
       else prefetch(tile);
     }
-    for (; tile < P.ntiles; tile += gridDim.x, ++it) {
+    for (; tile < tr.end; tile += tr.step, ++it) {
       const int buf = it & 1, use = it >> 1;
       const TileCoord c = tile_coord(P, tile, pl);
       if (kind) {
@@ -804,9 +827,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       // a NaN or an infinity anywhere in the pencil: every output of the pencil is NaN (the
       // epilogue sees kBadTau); its digits are written as zeros
       const bool bad_pencil = emax >= nonfinite_exp(TI(0));
-      if (tile + (int)gridDim.x < P.ntiles) {
-        if (kind) { if (tid == 0) tma_issue(tile + gridDim.x); }
-        else prefetch(tile + gridDim.x);
+      if (tile + tr.step < tr.end) {
+        if (kind) { if (tid == 0) tma_issue(tile + tr.step); }
+        else prefetch(tile + tr.step);
       }
       // A[buf] must be free: the MMAs of its previous use have completed
       if (use > 0 && !mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1), WL)) failed = true;
@@ -947,7 +970,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     constexpr int kExLo = sizeof(TO) == 8 ? (TFM ? -870 : -1022) : -126;
     constexpr int kExHi = sizeof(TO) == 8 ? (TFM ? 1000 : 969) : 127;
     int it = 0, pit = 0;
-    for (int tile = blockIdx.x; tile < P.ntiles && !failed; tile += gridDim.x, ++it) {
+    const TileRange tr = tile_range(P);
+    for (int tile = tr.first; tile < tr.end && !failed; tile += tr.step, ++it) {
       const TileCoord c = tile_coord(P, tile, pl);
       const bool interior = c.valid && P.int_lo1 <= c.t1 && c.t1 < P.int_hi1 && P.int_lo2 <= c.t2 && c.t2 < P.int_hi2;
       if (!mbar_wait_bounded(meta_full(it & 7), (uint32_t)((it >> 3) & 1), WL)) { failed = true; break; }
@@ -1085,8 +1109,20 @@ struct DenseGroup {
   DenseOp bop[3][2], bopI[3][2], bhalo0[3], bhaloI[3];
 };
 
+// Launch choices of the autotuner: per request (fields, ops, precision, iterations, entry
+// point) and per launch of it, the staging of the input tiles (0 TMA where the tile is a box,
+// 1 cp.async) and the tile order (0 interleaved, 1 contiguous runs), with the times measured.
+struct TuneRec {
+  int staging = 0, order = 0;
+  float ms[4] = {-1, -1, -1, -1};  // [staging * 2 + order]
+  std::string stage;
+};
 struct DenseState {
   std::vector<DenseGroup> groups;
+  std::map<std::string, std::vector<TuneRec>> tuned;
+  bool tuning = false;             // cfd_autotune in progress: every launch tries its candidates
+  std::string key;                 // the request of the current call
+  int launch = 0;                  // launches of the current call so far
 };
 
 DenseState *state_of(cfd_blocks_s *B) { return reinterpret_cast<DenseState *>(B->dense_state); }
@@ -1349,6 +1385,62 @@ void plan_tma(DenseParams &P, size_t elem) {
   P.tma_zstep = d0;
 }
 
+// Launch one stage with the choices the autotuner made for it (TMA staging and interleaved
+// tiles by default); during cfd_autotune, launch every candidate three times, time the last two
+// with events on the stream, and keep the fastest.  Repeated launches of a stage are idempotent
+// (a stage never reads what it writes), and every candidate computes the same outputs.
+cfd_status launch_stage(DenseState *ds, const DenseParams &P, int KP, int S, int L, size_t ein, bool f32,
+                        unsigned grid, cudaStream_t st) {
+  auto launch = [&](const DenseParams &Q) -> cfd_status {
+    const size_t smem = dense_smem(KP, S, Q.rows, ein, Q.tma_boxes);
+    if (!Q.in_field)
+      return f32 ? launch_types<double, float>(Q, KP, S, L, smem, grid, st)
+                 : launch_types<double, double>(Q, KP, S, L, smem, grid, st);
+    return f32 ? launch_types<float, float>(Q, KP, S, L, smem, grid, st)
+               : launch_types<double, double>(Q, KP, S, L, smem, grid, st);
+  };
+  auto configure = [&](int staging, int order) {
+    DenseParams Q = P;
+    Q.tile_order = order;
+    Q.tiles_per_cta = (Q.ntiles + (int)grid - 1) / (int)grid;
+    if (staging == 0) plan_tma(Q, ein);
+    else { Q.tma_kind = 0; Q.tma_boxes = 0; }
+    return Q;
+  };
+  const int idx = ds->launch++;
+  std::vector<TuneRec> &recs = ds->tuned[ds->key];
+  if (!ds->tuning) {
+    const bool have = idx < (int)recs.size();
+    return launch(configure(have ? recs[idx].staging : 0, have ? recs[idx].order : 0));
+  }
+  if ((int)recs.size() <= idx) recs.resize(idx + 1);
+  TuneRec &r = recs[idx];
+  const char axis = "zyx"[P.axis];
+  r.stage = std::string(P.in_field ? "S_" : "T_") + axis + (P.seg_mode[0][0] == 4 ? " halo" : "");
+  const int nstaging = configure(0, 0).tma_kind ? 2 : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cfd_status s = cuda_fail(cudaEventCreate(&e0), "cudaEventCreate");
+  if (s == CFD_OK) s = cuda_fail(cudaEventCreate(&e1), "cudaEventCreate");
+  float best = 1e30f;
+  for (int stg = 0; stg < nstaging && s == CFD_OK; ++stg)
+    for (int ord = 0; ord < 2 && s == CFD_OK; ++ord) {
+      const DenseParams Q = configure(stg, ord);
+      s = launch(Q);
+      if (s == CFD_OK) s = cuda_fail(cudaEventRecord(e0, st), "cudaEventRecord");
+      for (int k = 0; k < 2 && s == CFD_OK; ++k) s = launch(Q);
+      if (s == CFD_OK) s = cuda_fail(cudaEventRecord(e1, st), "cudaEventRecord");
+      if (s == CFD_OK) s = cuda_fail(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float ms = 0;
+      if (s == CFD_OK) s = cuda_fail(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      if (s != CFD_OK) break;
+      r.ms[stg * 2 + ord] = ms / 2;
+      if (ms < best) { best = ms; r.staging = stg; r.order = ord; }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return s;
+}
+
 }  // namespace
 
 struct DensePlanSizes {
@@ -1391,6 +1483,9 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
   }
   DenseState *ds = state_of(B);
   if (!ds) { set_error("dense: operators were not built at bind"); return CFD_ERR_UNSUPPORTED; }
+  ds->key = "apply nf=" + std::to_string(nf) + " ops=" + std::to_string(mask) + " prec=" + std::to_string((int)prec) +
+            " n_iter=" + std::to_string(n_iter);
+  ds->launch = 0;
   const int S = slices_of(prec, B->dtype), L = levels_of(prec, B->dtype);
   const DensePlanSizes z = dense_sizes(B, nf, mask, n_iter);
   double *gy = (double *)(((uintptr_t)work + 255) & ~(uintptr_t)255);
@@ -1458,13 +1553,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       P.tiles_per_job = (np + kTile - 1) / kTile;
       P.ntiles = P.tiles_per_job * P.nblk * P.nf;
       const unsigned grid = (unsigned)std::min(P.ntiles, sms);
-      plan_tma(P, ein);
-      const size_t smem = dense_smem(G.Kp, S, P.rows, ein, P.tma_boxes);
-      if (!P.in_field)
-        return f32 ? launch_types<double, float>(P, G.Kp, S, L, smem, grid, st)
-                   : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
-      return f32 ? launch_types<float, float>(P, G.Kp, S, L, smem, grid, st)
-                 : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
+      return launch_stage(ds, P, G.Kp, S, L, ein, f32, grid, st);
     };
     // segments: (degree, mode, op); passes of at most 32 rows
     auto iterating = [&](int box) { return n_iter > 0 && !G.cyc[box]; };
@@ -1646,6 +1735,9 @@ cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void 
   }
   DenseState *ds = state_of(B);
   if (!ds) { set_error("dense: operators were not built at bind"); return CFD_ERR_UNSUPPORTED; }
+  ds->key = "biased nf=" + std::to_string(nf) + " mode=" + std::to_string(mode) + " naxes=" + std::to_string(naxes) +
+            " prec=" + std::to_string((int)prec) + " n_iter=" + std::to_string(n_iter);
+  ds->launch = 0;
   const size_t need = dense_biased_workspace(B, nf, n_iter, mode == 2);
   if (!work || work_bytes < need) { set_error("biased path: workspace too small (see cfd_biased_workspace)"); return CFD_ERR_ARG; }
   const int S = slices_of(prec, B->dtype), L = levels_of(prec, B->dtype);
@@ -1706,10 +1798,7 @@ cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void 
       P.tiles_per_job = (np + kTile - 1) / kTile;
       P.ntiles = P.tiles_per_job * P.nblk * P.nf;
       const unsigned grid = (unsigned)std::min(P.ntiles, sms);
-      plan_tma(P, ein_b);
-      const size_t smem = dense_smem(G.Kp, S, P.rows, ein_b, P.tma_boxes);
-      return f32 ? launch_types<float, float>(P, G.Kp, S, L, smem, grid, st)
-                 : launch_types<double, double>(P, G.Kp, S, L, smem, grid, st);
+      return launch_stage(ds, P, G.Kp, S, L, ein_b, f32, grid, st);
     };
     for (int i = 0; i < naxes; ++i) {
       const int box = axes[i];
@@ -1782,3 +1871,35 @@ extern "C" cfd_status cfd_debug_set_wait_limit(long long cycles) {
   cfd::g_wait_limit = cycles > 0 ? cycles : cfd::kWaitLimit;
   return CFD_OK;
 }
+
+namespace cfd {
+// Autotuning hooks (api.cpp exposes them): switch the tuning mode of a handle, and describe the
+// choices made so far as JSON.
+void dense_set_tuning(cfd_blocks_s *B, bool on) {
+  DenseState *ds = state_of(B);
+  if (ds) ds->tuning = on;
+}
+std::string dense_tuning_report(cfd_blocks_s *B) {
+  DenseState *ds = state_of(B);
+  std::string o = "{";
+  if (ds) {
+    bool first = true;
+    for (const auto &kv : ds->tuned) {
+      o += std::string(first ? "" : ", ") + "\"" + kv.first + "\": [";
+      first = false;
+      for (size_t i = 0; i < kv.second.size(); ++i) {
+        const TuneRec &r = kv.second[i];
+        char buf[512];
+        snprintf(buf, sizeof buf,
+                 "%s{\"stage\": \"%s\", \"staging\": \"%s\", \"order\": \"%s\", \"ms\": {\"tma/interleaved\": %.5f, "
+                 "\"tma/contiguous\": %.5f, \"cp.async/interleaved\": %.5f, \"cp.async/contiguous\": %.5f}}",
+                 i ? ", " : "", r.stage.c_str(), r.staging ? "cp.async" : "tma", r.order ? "contiguous" : "interleaved",
+                 r.ms[0], r.ms[1], r.ms[2], r.ms[3]);
+        o += buf;
+      }
+      o += "]";
+    }
+  }
+  return o + "}";
+}
+}  // namespace cfd

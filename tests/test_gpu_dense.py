@@ -224,6 +224,38 @@ def test_tf32_one_product_measured_bound(lib, torch, NM, N):
         assert worst[op] < bound, (op, worst[op])
 
 
+@pytest.mark.parametrize("n_iter", [0, 1])
+def test_autotune_keeps_results_and_reports(lib, torch, n_iter):
+    """cfd_autotune runs the request once with every kernel under each candidate configuration
+    (TMA or cp.async staging, interleaved or contiguous tiles): the outputs are bit-identical to
+    cfd_apply's, every kernel of the request has a choice with its measured times, and cfd_apply
+    with the tuned choices gives the same outputs again."""
+    NM, N, g, nf = 64, 32, 4, 2
+    mesh, dx, exts, buf = uniform(NM, N, g, fields4(811)[:nf])
+    s = lib.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
+    B = lib.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, lib.CFD_F64)
+    prec = lib.CFD_TC_BF16_EXACT
+    ref = apply(lib, torch, B, buf, nf, lib.CFD_OP_ALL, prec, n_iter)
+    dev = torch.device("cuda", 0)
+    fields = torch.from_numpy(np.ascontiguousarray(buf)).to(dev)
+    out = torch.full((ref.size,), float("nan"), dtype=torch.float64, device=dev)
+    ws = lib.cfd_apply_workspace(B, nf, lib.CFD_OP_ALL, prec, n_iter)
+    work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
+    lib.cfd_autotune(B, fields, nf, lib.CFD_OP_ALL, prec, n_iter, out, work)
+    lib.cfd_sync_status(B)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    rep = lib.cfd_autotune_report(B)
+    (key,) = [k for k in rep if k.startswith("apply") and f"n_iter={n_iter}" in k]
+    stages = rep[key]
+    assert len(stages) == (6 if n_iter == 0 else 12)
+    for st in stages:
+        assert st["staging"] in ("tma", "cp.async") and st["order"] in ("interleaved", "contiguous")
+        chosen = st["ms"][f"{st['staging']}/{st['order']}"]
+        assert chosen > 0 and all(v < 0 or v >= chosen for v in st["ms"].values())
+    again = apply(lib, torch, B, buf, nf, lib.CFD_OP_ALL, prec, n_iter)
+    assert np.array_equal(again, ref)
+
+
 def box16_32():
     """16^3 coarse blocks with a 2:1 refined octant of 32^3 blocks on [0, 2pi)^3 (both sizes run on
     the tensor cores): the two-size layout of the 22-field workload, 56 + 8 blocks."""
