@@ -87,10 +87,13 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 
 # DRAM traffic of the dominant kernel per launch, from an ncu capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, path, n_iter); a workload
-# too large to capture is captured on its 128^3 variant with the same blocks and scaled by the
-# points (the per-block work is the same).  Values with their profile summary under profiles/.
-MEASURED_TRAFFIC = {}
+# (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the launches of one step), keyed
+# by (workload, path, n_iter).  Values with their profile summary under profiles/.
+MEASURED_TRAFFIC = {
+    # 256^3 as 512 blocks of 32^3, 4 FP64 fields, 9 ops: one-pass capture of the 6 k_dense
+    # launches of a step at full size (profiles/k_dense_tc_exact_cfd128_b32_f4.md)
+    ("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1755182891,
+}
 
 
 def scheme_descs(name: str = "Q13"):
@@ -792,11 +795,15 @@ def main():
                 "tensor_frac_of_bf16_peak": round(tcf / float(peaks.get("bf16_tflops", 1900.0)), 4) if tcf else None,
                 "traffic": MEASURED_TRAFFIC.get((args.workload, args.prec, n_iter)),
                 "algorithmic_bytes_per_launch": round(algorithmic_bytes(nint, nf, nops, elem) / max(nl / prof_steps, 1))}
+    if roof.get("traffic") and roof.get("unit") == "GB/s":
+        # the DRAM bytes the kernel actually moves per launch, over the same event time
+        dram = roof["traffic"] / (tl / max(nl, 1) * 1e-3) / 1e9
+        roof.update({"traffic_gbs": round(dram, 1), "traffic_frac": round(dram / roof["peak"], 4),
+                     "traffic_over_algorithmic": round(roof["traffic"] / roof["algorithmic_bytes_per_launch"], 3)})
     roof.update({"launches_per_step": nl / prof_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
                  "share_of_step": round(tl / ms_total, 4), "events_region": {"steps": prof_steps,
                                                                           "ms_per_step": round(ms_prof, 5)}})
 
-    # the FP64 banded solve on the same inputs: speed and max relative difference per (field, op)
     # The FP64 banded solve on the same inputs: speed and max relative difference per (field, op).
     # Two forms: the paper's symmetrised mixed derivatives (both orders, averaged) and one order,
     # the work the tensor-core path does (cfd_blocks_set_mixed_order; equal on these meshes to

@@ -775,18 +775,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       }
       asm volatile("cp.async.commit_group;");
     };
-    // staging address of element j of this thread's pencil
+    // staging address of element j of this thread's pencil, one formula for every staging kind
+    // (j is a constant in the unrolled loads, so each is an XOR and two multiply-adds, with no
+    // branch on the kind in the hot loop):
+    //   kind 0 (cp.async rows):        pl * pitch + j
+    //   kind 1 (TMA, 128-byte rows):   (j / XB) * 128 XB + pl * XB + ((j % XB) XOR (pl % 8) * VE),
+    //                                  i.e. the 16-byte chunk index XOR (row mod 8)
+    //   kinds 2, 3 (TMA boxes):        col_base + j * col_step
     const int n2 = P.n2;
     const int col_base = kind == 2 ? (pl / n2) * E * n2 + (pl % n2) : pl;       // kinds 2, 3
     const int col_step = kind == 2 ? n2 : kTile;
-    auto stg_index = [&](int j) -> int {
-      if (kind == 0) return pl * pitch + j;
-      if (kind == 1) {  // 128-byte rows, 16-byte chunk index XOR (row mod 8)
-        const int bx = j / XB, xo = j - bx * XB;
-        return bx * (kTile * XB) + pl * XB + (((xo / VE) ^ (pl & 7)) * VE) + (xo % VE);
-      }
-      return col_base + j * col_step;
-    };
+    constexpr int LVE = VE == 2 ? 1 : 2;  // log2(VE)
+    static_assert(XB == 8 * VE && (VE == 2 || VE == 4), "a 128-byte row holds 8 chunks of 16 bytes");
+    const int ib = kind == 0 ? pl * pitch : (kind == 1 ? pl * XB : col_base);
+    const int ihi = kind == 0 ? XB : (kind == 1 ? kTile * XB : XB * col_step);
+    const int ilo = kind <= 1 ? 1 : col_step;
+    const int ixr = kind == 1 ? (pl & 7) << LVE : 0;
+    auto stg_index = [&](int j) -> int { return ib + (j / XB) * ihi + ((j % XB) ^ ixr) * ilo; };
     const uint32_t lbo = 128, sbo = KP * 16;
     int it = 0, pit = 0;
     uint32_t last_bar = 0;  // thread 0: an MMA was issued
@@ -1018,21 +1023,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
         const int *rexp = s_rowexp + ps * 48 + r0;
         // rows in groups of 8 (fewer live registers); the pass buffer is released after the last group.
-        // A warp whose outputs all stay in the normal range takes the unchecked conversion.
+        // A warp whose outputs all stay in the normal range takes the unchecked conversion.  The
+        // groups run as a loop, not unrolled: one copy of the rebuild code per conversion keeps the
+        // epilogue's hot loop small next to the producers' in each sub-partition's instruction cache.
         const int rlo = ps ? rlo1 : rlo0, rhi = ps ? rhi1 : rhi0;
         const bool safe = !(wf || ws) || (!bad && ebase + rlo >= kExLo && ebase + rhi <= kExHi);
+        const bool vec = P.xvec != 0;
         if (__all_sync(0xffffffffu, safe)) {
-          if (RH == 16)
-            epilogue_rows<8, L + 1, TO, false, TFM>(taddr, (uint32_t)R, ebase, bad, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u,
-                                               srows, P.xvec != 0, gx, gyp);
-          epilogue_rows<8, L + 1, TO, false, TFM>(taddr + (RH - 8), (uint32_t)R, ebase, bad, rexp + (RH - 8), fb, f_ax, sb,
-                                             sstr, wf, ws, i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0, gx, gyp);
+#pragma unroll 1
+          for (int gq = RH == 16 ? 0 : 1; gq < 2; ++gq) {
+            const int o8 = gq ? RH - 8 : 0;
+            epilogue_rows<8, L + 1, TO, false, TFM>(taddr + o8, (uint32_t)R, ebase, bad, rexp + o8, fb, f_ax, sb, sstr,
+                                                    wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, srows, vec, gx, gyp);
+          }
         } else {
-          if (RH == 16)
-            epilogue_rows<8, L + 1, TO, true, TFM>(taddr, (uint32_t)R, ebase, bad, rexp, fb, f_ax, sb, sstr, wf, ws, i0, 0u,
-                                              srows, P.xvec != 0, gx, gyp);
-          epilogue_rows<8, L + 1, TO, true, TFM>(taddr + (RH - 8), (uint32_t)R, ebase, bad, rexp + (RH - 8), fb, f_ax, sb,
-                                            sstr, wf, ws, i0 + (RH - 8), t_empty(tb), srows, P.xvec != 0, gx, gyp);
+#pragma unroll 1
+          for (int gq = RH == 16 ? 0 : 1; gq < 2; ++gq) {
+            const int o8 = gq ? RH - 8 : 0;
+            epilogue_rows<8, L + 1, TO, true, TFM>(taddr + o8, (uint32_t)R, ebase, bad, rexp + o8, fb, f_ax, sb, sstr,
+                                                   wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, srows, vec, gx, gyp);
+          }
         }
       }
     }

@@ -1,4 +1,4 @@
-"""The allocation-free entry point cfd_apply_static, checked against cfd_apply.
+"""The allocation-free entry point cfd_apply_static, checked against the oracle and cfd_apply.
 
 Callers that cannot allocate device memory when they apply the operators
 (their host code owns all device memory, or their loop must not allocate or
@@ -10,7 +10,7 @@ import pytest
 
 from oracle import cfd as C
 from paper_2302_14858_gb300 import workloads as W
-from tests.helpers import desc, rel_max
+from tests.helpers import OPS, desc, oracle_sch, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -36,21 +36,24 @@ def _fields(NM, N, g, seeds):
     for s in seeds:
         r = W.rng(s)
         f = W.Sum([W.sine_sum(r, 8, 1, 12), W.gaussian(r, 0.1)])
-        exts.append(C.ghost_fill_3d(f(X, Y, Z), N, g).reshape(mesh.nblocks, E, E, E))
-    return mesh, np.stack(exts, axis=1).reshape(-1)
+        exts.append(C.ghost_fill_3d(f(X, Y, Z), N, g))
+    flat = np.stack([e.reshape(mesh.nblocks, E, E, E) for e in exts], axis=1).reshape(-1)
+    return mesh, flat, exts
 
 
 def test_static_scratch_matches_workspace_path_twice(env):
     cfd, torch = env
     NM, N, g, nf = 64, 16, 4, 2
-    mesh, buf1 = _fields(NM, N, g, (501, 502))
-    _, buf2 = _fields(NM, N, g, (503, 504))
+    dx = 2 * np.pi / NM
+    mesh, buf1, ext1 = _fields(NM, N, g, (501, 502))
+    _, buf2, ext2 = _fields(NM, N, g, (503, 504))
     s = cfd.cfd_scheme_create(desc("Q13_1_d1"), desc("Q13_1_d2"))
     B = cfd.cfd_blocks_bind(s, mesh.n, mesh.dx, mesh.neighbors, g, cfd.CFD_F64)
     nout = mesh.nblocks * nf * 9 * N ** 3
     ws = cfd.cfd_apply_workspace(B, nf, cfd.CFD_OP_ALL, cfd.CFD_FP64_BANDED, 0)
     work = torch.empty(ws, dtype=torch.uint8, device="cuda")
-    for buf in (buf1, buf2):          # two calls in a row, different data
+    s1, s2 = oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2")
+    for buf, exts in ((buf1, ext1), (buf2, ext2)):     # two calls in a row, different data
         f = torch.from_numpy(buf).cuda()
         ref = torch.empty(nout, dtype=torch.float64, device="cuda")
         got = torch.full((nout,), float("nan"), dtype=torch.float64, device="cuda")
@@ -61,7 +64,9 @@ def test_static_scratch_matches_workspace_path_twice(env):
         o = got.cpu().numpy().reshape(mesh.nblocks, nf, 9, -1)
         assert np.isfinite(o).all()
         for q in range(nf):
-            for i in range(9):
+            want = C.apply_uniform(exts[q], s1, s2, (dx, dx, dx), N, g, OPS, 0)
+            for i, op in enumerate(OPS):
+                assert rel_max(o[:, q, i], want[op].reshape(mesh.nblocks, -1)) < TOL64, (q, op)
                 assert rel_max(o[:, q, i], r[:, q, i]) < TOL64
 
 
