@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 
+#include <vector>
+
 #include "cfd_internal.h"
 
 namespace cfd {
@@ -26,14 +28,14 @@ struct DenseParams {
   int nseg[2];               // operators (segments of N rows) per pass
   const void *seg_img[2][2];  // operator images of the pass's segments (BF16 digits or TF32)
   const int *seg_exp[2][2];
-  int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both, 4 halo rows
+  int seg_mode[2][2];        // -1 skip, 0 final (interior pencils), 2 scratch, 3 both
   int seg_op[2][2];          // op index in the output for final stores
   int tiles_per_job, ntiles; // 128-pencil tiles per (block, field); all tiles of the stage
   int tile_order, tiles_per_cta;  // 0: tile = CTA + k grid; 1: contiguous runs of tiles_per_cta
   int seg_rows;              // operator rows per segment (N, or 16 for a halo pass)
   int kext;                  // K values loaded per pencil: N + 2g, or N + 2g + 4 with halo columns
   const double *halo_in;     // [nblocks][nf][n1 n2][4]: previous iterate at rows 1, N-2 per degree (x dx^d)
-  double *halo_out;          // same layout, written by a halo pass (seg_mode 4)
+  double *halo_out;          // same layout, written by a halo pass (k_halo_rows)
   const int *nbr;            // [nblocks][26] neighbour table
   int halo_deg_mask;         // degrees whose halo columns are filled (bit d-1)
   int xrow;                  // x-axis stage with 16-byte aligned pencil rows: chunked row copies
@@ -54,6 +56,21 @@ struct DenseParams {
   int *status;
   long long wait_limit;      // clock cycles a main-loop wait may take before it latches CFD_ERR_TIMEOUT
 };
+
+// The four operator rows of one halo pass of the hybrid iteration (Eq. iter_center_P: rows 1
+// and N-2 per degree; Eq. iter_left_X: the biased rows the neighbours read), each coefficient
+// as an FP32 pair c = h + l (to ~2^-48 relative), for the compensated CUDA-core kernel of
+// halo_rows.cu.  Columns: the N + 2g pencil values, then the 4 halo columns of the previous
+// iterate (zero in the first pass).
+struct HaloRows {
+  float h[48][4], l[48][4];  // [column][row]
+};
+// rows 0..3 of the row-major rows x cols matrix M (cols <= 48)
+void halo_rows_from(const std::vector<long double> &M, int cols, HaloRows &R);
+// One halo pass of a dense stage on the CUDA cores: for every pencil of the stage (the
+// addressing of P, as k_dense reads it), the 4 rows of R applied to the pencil (and, with
+// P.halo_in, to the neighbours' previous iterate), written to P.halo_out.
+cfd_status halo_rows_launch(const DenseParams &P, const HaloRows &R, bool f32_in, cudaStream_t st);
 
 cfd_status dense_bind(cfd_blocks_s *B);
 void dense_set_tuning(cfd_blocks_s *B, bool on);

@@ -23,16 +23,10 @@
 // sum_j |D_ij f_j|, i.e. FP64-level for these operators.  (S, L) = (2, 1) is
 // the 3-product hi/lo split.
 //
-// Kernel structure (one CTA = one tile of 128 pencils, 4 warps):
-//   1. warp 0 allocates 256 TMEM columns;
-//   2. all threads copy the digit images of D for this stage into shared
-//      memory (canonical K-major, no swizzle, 8x16-byte core matrices);
-//   3. thread t loads pencil t, splits it into 5 BF16 digit rows of the A
-//      operand in shared memory;
-//   4. one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate) for
-//      every (s, t) pair and K step, commits to an mbarrier;
-//   5. all threads wait (bounded), read their TMEM lane (= pencil) with
-//      tcgen05.ld, rebuild each output and store it.
+// Kernel structure: a persistent, warp-specialised CTA per SM (producers stage
+// and split the pencils of a tile, one thread issues tcgen05.mma, epilogue warps
+// read TMEM and rebuild the outputs), described at k_dense below.  The halo
+// passes of the hybrid iteration run on the CUDA cores (halo_rows.cu).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -412,8 +406,8 @@ __device__ __forceinline__ long long stride_of(int axis, long long s0, long long
 // ------------------------------------------------------------------ the kernel
 //
 // Persistent, one CTA of 16 warps per SM, warp-specialised:
-//   warps 0-7   producers: cp.async the next tile's pencils into a staging
-//               buffer, split the current one into 5 digit rows of A[buf]
+//   warps 0-7   producers: stage the next tile's pencils (TMA boxes, or
+//               cp.async), split the current one into 5 digit rows of A[buf]
 //               (two A buffers), publish the pencil scales (meta_full); then
 //               thread 0 issues tcgen05.mma for every pass of the tile into
 //               one of three TMEM pass buffers (t_full on commit) and frees
@@ -443,7 +437,7 @@ template <int RH, int LEV, typename TO, bool checked, int TFM>
 __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_stride, int ebase, bool bad,
                                               const int *rowexp, TO *fin_base, long long fin_stride, double *sc_base,
                                               long long sc_stride, bool write_fin, bool write_sc, int i0,
-                                              uint32_t t_empty_addr, int sc_rows, bool vec, double *sc_x,
+                                              uint32_t t_empty_addr, bool vec, double *sc_x,
                                               double *sc_y) {
   uint32_t acc[LEV][RH];
 #pragma unroll
@@ -495,7 +489,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
         }
       };
       TO val;
-      double dv = 0.0;  // the FP64 value the intermediates and halo values keep
+      double dv = 0.0;  // the FP64 value the intermediates keep
       if constexpr (TFM) {
         // TF32 form: one FP32 accumulator per output, scaled by 2^(rowexp + etau)
         const float a = __uint_as_float(acc[0][c]);
@@ -520,7 +514,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
       }
       o[u] = val;
       const long long i = i0 + c;
-      if (write_sc && i < sc_rows) {
+      if (write_sc) {
         sc_base[i * sc_stride] = dv;
         if (sc_x) sc_x[i * sc_stride] = dv;  // the face neighbour's ghost column
         if (sc_y) sc_y[i * sc_stride] = dv;
@@ -604,7 +598,11 @@ __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, 
 
 // TFM = 1: the one-product TF32 form (S = 1, L = 0): A = the pencils scaled by tau and rounded
 // to TF32, B = the TF32 image of D, one kind::tf32 MMA chain per pass, FP32 accumulators.
-template <typename TI, typename TO, int KP, int S, int L, int TFM>
+//
+// ITER = 1: the final pass of an iterated stage (halo_in set), whose TMA-staged tiles take the
+// neighbours' previous iterate as 4 extra columns.  A separate instantiation keeps that code out
+// of the closed passes' producer loop (measured 5 % slower with it there).
+template <typename TI, typename TO, int KP, int S, int L, int TFM, bool ITER>
 __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int EB = TFM ? 4 : 2;  // bytes per operand element (TF32 or BF16)
@@ -783,7 +781,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     //                                  i.e. the 16-byte chunk index XOR (row mod 8)
     //   kinds 2, 3 (TMA boxes):        col_base + j * col_step
     const int n2 = P.n2;
-    const int col_base = kind == 2 ? (pl / n2) * E * n2 + (pl % n2) : pl;       // kinds 2, 3
+    // (a kind-2 box is [t1][kext][x]: kext rows along y, the 4 halo columns of an iterated pass
+    // included)
+    const int col_base = kind == 2 ? (pl / n2) * P.kext * n2 + (pl % n2) : pl;  // kinds 2, 3
     const int col_step = kind == 2 ? n2 : kTile;
     constexpr int LVE = VE == 2 ? 1 : 2;  // log2(VE)
     static_assert(XB == 8 * VE && (VE == 2 || VE == 4), "a 128-byte row holds 8 chunks of 16 bytes");
@@ -804,12 +804,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     for (; tile < tr.end; tile += tr.step, ++it) {
       const int buf = it & 1, use = it >> 1;
       const TileCoord c = tile_coord(P, tile, pl);
+      // An iterated pass staged by TMA: the neighbours' previous iterate goes into staging
+      // columns E .. E+3 of this pencil (the box reads zeros or data it overwrites there).  Each
+      // of the pencil's threads writes the columns of its own K chunks, which only it reads.
+      double hq[4] = {0.0, 0.0, 0.0, 0.0};
+      const bool tma_halo = ITER && kind && P.halo_in && c.valid;
+      if (tma_halo) {
+        const int ez = P.axis == 0, ey = P.axis == 1, ex = P.axis == 2;
+        const long long pp = (long long)tile_pencil(P, tile, pl);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int d = m >> 1, jq = m & 1;
+          if ((((E + m) >> 3) % kParts) != half || !((P.halo_deg_mask >> d) & 1)) continue;
+          const int nb = P.nbr[c.b * 26 + dir_index_dev(jq ? ez : -ez, jq ? ey : -ey, jq ? ex : -ex)];
+          hq[m] = P.halo_in[(((long long)nb * P.nf + c.q) * (long long)(P.n1 * P.n2) + pp) * 4 + 2 * d + (jq ? 0 : 1)];
+        }
+      }
       if (kind) {
         if (!mbar_wait_bounded(stg_full, (uint32_t)(it & 1), WL)) failed = true;
         else if (tid == 0) tma_pending = false;
       } else {
         asm volatile("cp.async.wait_all;");
         producer_sync();
+      }
+      if (tma_halo && !failed) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if ((((E + m) >> 3) % kParts) == half) stg[stg_index(E + m)] = TI(hq[m]);
       }
       TI v[CPP][8];
       int em = 0;
@@ -991,25 +1012,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const int sg = r0 / P.seg_rows, i0 = r0 - sg * P.seg_rows;
         const int mode = P.seg_mode[ps][sg];
         const bool wf = (mode == 0 || mode == 3) && interior;
-        // mode 4 (halo pass): rows 0-3 of the first half go to the pencil's 4 halo values
-        const bool halo = mode == 4;
-        const bool ws = (mode == 2 || mode == 3 || (halo && ehalf == 0)) && c.valid;
+        const bool ws = (mode == 2 || mode == 3) && c.valid;
         TO *fb = static_cast<TO *>(P.out);
         double *sb = P.scratch_out;
         if (wf)
           fb += (long long)P.nf * P.nops * (P.contig ? P.int0 + (long long)c.lb * n3 : P.intpre[c.b]) +
                 ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
                 (long long)(c.t1 - P.int_lo1) * f_t1 + (long long)(c.t2 - P.int_lo2) * f_t2;
-        if (ws && halo)
-          sb = P.halo_out + (((long long)c.b * P.nf + c.q) * (long long)(P.n1 * P.n2) + tile_pencil(P, tile, pl)) * 4;
-        else if (ws)
+        if (ws)
           sb += ((long long)c.lb * P.nf + c.q) * (long long)P.sc_box + (long long)(sc_s1 + c.t1) * c_t1 +
                 (long long)(sc_s2 + c.t2) * c_t2;
-        const long long sstr = halo ? 1 : c_ax;
-        const int srows = halo ? 4 : 1 << 30;
+        const long long sstr = c_ax;
         // interior pencils near an x (y) face also fill the neighbour's ghost column (row)
         double *gx = nullptr, *gyp = nullptr;
-        if (ws && !halo && P.ghost_x) {
+        if (ws && P.ghost_x) {
           const int xs = sc_s2 + c.t2;  // t2 is the x axis in the stages that write intermediates
           const long long jump = (long long)P.nf * (long long)P.sc_box;
           if (xs < 2 * g) gx = sb + (long long)(P.nl[c.lb * 4 + 0] - c.lb) * jump + N;
@@ -1034,14 +1050,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
           for (int gq = RH == 16 ? 0 : 1; gq < 2; ++gq) {
             const int o8 = gq ? RH - 8 : 0;
             epilogue_rows<8, L + 1, TO, false, TFM>(taddr + o8, (uint32_t)R, ebase, bad, rexp + o8, fb, f_ax, sb, sstr,
-                                                    wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, srows, vec, gx, gyp);
+                                                    wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, vec, gx, gyp);
           }
         } else {
 #pragma unroll 1
           for (int gq = RH == 16 ? 0 : 1; gq < 2; ++gq) {
             const int o8 = gq ? RH - 8 : 0;
             epilogue_rows<8, L + 1, TO, true, TFM>(taddr + o8, (uint32_t)R, ebase, bad, rexp + o8, fb, f_ax, sb, sstr,
-                                                   wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, srows, vec, gx, gyp);
+                                                   wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, vec, gx, gyp);
           }
         }
       }
@@ -1057,15 +1073,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
 template <typename TI, typename TO, int KP>
 cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned grid, cudaStream_t st) {
   void (*fn)(const __grid_constant__ DenseParams);
-  if (S == 5 && L == 4) fn = k_dense<TI, TO, KP, 5, 4, 0>;
-  else if (S == 2 && L == 1) fn = k_dense<TI, TO, KP, 2, 1, 0>;
-  else if (S == 1 && L == 0) fn = k_dense<TI, TO, KP, 1, 0, 1>;
+  const bool it = P.halo_in != nullptr;
+  if (S == 5 && L == 4) fn = it ? k_dense<TI, TO, KP, 5, 4, 0, true> : k_dense<TI, TO, KP, 5, 4, 0, false>;
+  else if (S == 2 && L == 1) fn = it ? k_dense<TI, TO, KP, 2, 1, 0, true> : k_dense<TI, TO, KP, 2, 1, 0, false>;
+  else if (S == 1 && L == 0) fn = it ? k_dense<TI, TO, KP, 1, 0, 1, true> : k_dense<TI, TO, KP, 1, 0, 1, false>;
   else { set_error("dense: unsupported slice configuration"); return CFD_ERR_UNSUPPORTED; }
   // The shared-memory opt-in is set once per device and instantiation (and raised when a
   // launch needs more), so that later calls issue nothing but the launch: a stream being
   // captured into a CUDA graph sees only kernel nodes.
-  static size_t opted[3][64] = {};  // [slice configuration][device]
-  const int v = S == 5 ? 0 : (S == 2 ? 1 : 2);
+  static size_t opted[6][64] = {};  // [slice configuration, iterated][device]
+  const int v = (S == 5 ? 0 : (S == 2 ? 1 : 2)) + (it ? 3 : 0);
   int dev = 0;
   cfd_status s = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
   if (s != CFD_OK) return s;
@@ -1108,15 +1125,17 @@ struct DenseGroup {
   bool cyc[3] = {false, false, false};
   DenseOp op[3][2];      // [axis box index z,y,x][degree-1]: closed operator [0]D, dx-scaled
   DenseOp opI[3][2];     // iterated operator [D1 | c- | c+] with halo columns, dx-scaled
-  DenseOp halo0[3];      // rows 1 and N-2 of [0]D per degree (16 rows), unscaled
-  DenseOp haloI[3];      // rows 1 and N-2 of the iterated operator (16 rows), unscaled
+  // rows 1 and N-2 per degree of [0]D and of the iterated operator (unscaled), for the halo
+  // passes on the CUDA cores
+  HaloRows hr0[3], hrI[3];
   bool faces_x = false, faces_y = false;  // every block has both x (y) face neighbours
   int *d_nl = nullptr;   // device [nblk][4]: local indices of the x-, x+, y-, y+ neighbours
   // biased first-degree operators ([box][0 left-biased S+, 1 right-biased S-]), dx-scaled:
   // closed (or cyclic) [0]D, iterated [D1 | coupling in halo column E (S+) or E+3 (S-)];
   // halo images (unscaled): row 1 = S+ row N-kc, row 2 = S- row kc-1
   bool biased = false;
-  DenseOp bop[3][2], bopI[3][2], bhalo0[3], bhaloI[3];
+  DenseOp bop[3][2], bopI[3][2];
+  HaloRows bhr0[3], bhrI[3];
 };
 
 // Launch choices of the autotuner: per request (fields, ops, precision, iterations, entry
@@ -1226,9 +1245,8 @@ cfd_status dense_bind(cfd_blocks_s *B) {
         }
       }
       if (!cyc && G.iter_ok) {
-        cfd_status s = upload_op(B, H0, 16, E, G.Kp, G.halo0[box]);
-        if (s == CFD_OK) s = upload_op(B, HI, 16, G.Kp, G.Kp, G.haloI[box]);
-        if (s != CFD_OK) return s;
+        halo_rows_from(H0, E, G.hr0[box]);
+        halo_rows_from(HI, G.Kp, G.hrI[box]);
       }
       if (B->biased.present && B->biased.kc <= N) {
         const BiasedCoef &bc = B->biased;
@@ -1256,9 +1274,8 @@ cfd_status dense_bind(cfd_blocks_s *B) {
           BHI[(size_t)(1 + side) * G.Kp + hcol] = cp[krow];
         }
         if (!cyc && G.iter_ok) {
-          cfd_status s = upload_op(B, BH0, 16, E, G.Kp, G.bhalo0[box]);
-          if (s == CFD_OK) s = upload_op(B, BHI, 16, G.Kp, G.Kp, G.bhaloI[box]);
-          if (s != CFD_OK) return s;
+          halo_rows_from(BH0, E, G.bhr0[box]);
+          halo_rows_from(BHI, G.Kp, G.bhrI[box]);
         }
         G.biased = true;
       }
@@ -1352,8 +1369,9 @@ EncodeTiledFn tensor_map_encoder() {
 void plan_tma(DenseParams &P, size_t elem) {
   P.tma_kind = 0;
   P.tma_boxes = 0;
-  if (P.halo_in) return;  // iterated passes add halo columns per pencil
-  const int n2 = P.n2, E = P.N + 2 * P.g;
+  // An iterated pass (halo_in) takes kext = E + 4 values per pencil: the boxes cover kext along
+  // the pencil axis, and the producers write the 4 halo columns into the staged tile.
+  const int n2 = P.n2, E = P.N + 2 * P.g, K = P.kext;
   if ((n2 != 16 && n2 != 32) || (P.n1 * n2) % kTile != 0) return;
   if (P.in_field && !P.contig) return;
   const int d0 = P.in_dims[0], d1 = P.in_dims[1], d2 = P.in_dims[2];
@@ -1373,17 +1391,17 @@ void plan_tma(DenseParams &P, size_t elem) {
   const int xb = (int)(128 / elem);
   if (P.axis == 2) {  // t1 = z, t2 = y
     kind = 1;
-    boxes = (E + xb - 1) / xb;
+    boxes = (K + xb - 1) / xb;
     box[0] = (cuuint32_t)xb; box[1] = (cuuint32_t)n2; box[2] = (cuuint32_t)(kTile / n2);
     swz = CU_TENSOR_MAP_SWIZZLE_128B;
   } else if (P.axis == 1) {  // t1 = z, t2 = x
     kind = 2;
     boxes = 1;
-    box[0] = (cuuint32_t)n2; box[1] = (cuuint32_t)E; box[2] = (cuuint32_t)(kTile / n2);
+    box[0] = (cuuint32_t)n2; box[1] = (cuuint32_t)K; box[2] = (cuuint32_t)(kTile / n2);
   } else {  // t1 = y, t2 = x
     kind = 3;
     boxes = 1;
-    box[0] = (cuuint32_t)n2; box[1] = (cuuint32_t)(kTile / n2); box[2] = (cuuint32_t)E;
+    box[0] = (cuuint32_t)n2; box[1] = (cuuint32_t)(kTile / n2); box[2] = (cuuint32_t)K;
   }
   const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   if (enc(&P.tmap, dt, 3, const_cast<char *>(base), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
@@ -1426,7 +1444,7 @@ cfd_status launch_stage(DenseState *ds, const DenseParams &P, int KP, int S, int
   if ((int)recs.size() <= idx) recs.resize(idx + 1);
   TuneRec &r = recs[idx];
   const char axis = "zyx"[P.axis];
-  r.stage = std::string(P.in_field ? "S_" : "T_") + axis + (P.seg_mode[0][0] == 4 ? " halo" : "");
+  r.stage = std::string(P.in_field ? "S_" : "T_") + axis;
   const int nstaging = configure(0, 0).tma_kind ? 2 : 1;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cfd_status s = cuda_fail(cudaEventCreate(&e0), "cudaEventCreate");
@@ -1592,26 +1610,19 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
     // [n_iter-1] (the values the neighbours need at their k^c nodes) into a
     // ping-pong buffer; the final pass applies the iterated operator with
     // those values as four extra K columns.  Each pass is one launch: all
-    // blocks of iterate i are complete before any block reads them.
+    // blocks of iterate i are complete before any block reads them.  The halo
+    // passes are four dot products per pencil and run on the CUDA cores in
+    // compensated FP32 (halo_rows.cu), at a fraction of a tensor-core pass.
     auto run_stage = [&](DenseParams P, int box) -> cfd_status {
       if (!iterating(box)) return run(P);
       DenseParams H = P;
-      H.passes = 1;
-      H.rows = 16;
-      H.seg_rows = 16;
-      H.nseg[0] = 1;
-      H.nseg[1] = 0;
-      H.seg_mode[0][0] = 4;
-      H.seg_op[0][0] = 0;
       H.scratch_out = nullptr;
       for (int it = 0; it < n_iter; ++it) {
-        const DenseOp &o = it == 0 ? G.halo0[box] : G.haloI[box];
-        H.seg_img[0][0] = o.image(prec == CFD_TC_TF32);
-        H.seg_exp[0][0] = o.rowexp;
         H.halo_in = it == 0 ? nullptr : halo[(it - 1) & 1];
         H.halo_out = halo[it & 1];
         H.kext = it == 0 ? E : E + 4;
-        cfd_status r = run(H);
+        cfd_status r = halo_rows_launch(H, it == 0 ? G.hr0[box] : G.hrI[box],
+                                        H.in_field && B->dtype == CFD_F32, st);
         if (r != CFD_OK) return r;
       }
       P.halo_in = halo[(n_iter - 1) & 1];
@@ -1734,8 +1745,9 @@ size_t dense_biased_workspace(const cfd_blocks_s *B, int nf, int n_iter, bool ad
 // read-modify-write of the output to the epilogue; measured slower, 9.5 vs 5.7 ms at 256^3.)
 // The operators are
 // the dense forms of the block systems of Eqs. closure_left_X / iter_left_X (bind time); the
-// iteration reuses the halo passes of the centred path with the biased halo images (slot 1:
-// S+ at row N-kc, read by the upper neighbour; slot 2: S- at row kc-1, read by the lower one).
+// iteration runs the halo passes of the centred path (k_halo_rows) with the biased halo rows
+// (slot 1: S+ at row N-kc, read by the upper neighbour; slot 2: S- at row kc-1, read by the
+// lower one).
 cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void *beta, const int *axes, int naxes,
                         int mode, cfd_precision prec, int n_iter, void *out, int out_nops, int out_opidx,
                         bool accum_all, void *work, size_t work_bytes, cudaStream_t st) {
@@ -1845,22 +1857,14 @@ cfd_status dense_biased(cfd_blocks_s *B, const void *fields, int nf, const void 
         }
       }
       if (iter) {
+        // halo passes on the CUDA cores (halo_rows.cu), as for the centred operators
         DenseParams H = P;
-        H.passes = 1;
-        H.rows = 16;
-        H.seg_rows = 16;
-        H.nseg[0] = 1;
-        H.nseg[1] = 0;
-        H.seg_mode[0][0] = 4;
-        H.seg_op[0][0] = 0;
         for (int it = 0; it < n_iter; ++it) {
-          const DenseOp &o = it == 0 ? G.bhalo0[box] : G.bhaloI[box];
-          H.seg_img[0][0] = o.image(prec == CFD_TC_TF32);
-          H.seg_exp[0][0] = o.rowexp;
           H.halo_in = it == 0 ? nullptr : halo[(it - 1) & 1];
           H.halo_out = halo[it & 1];
           H.kext = it == 0 ? E : E + 4;
-          if ((s = run(H)) != CFD_OK) return s;
+          if ((s = halo_rows_launch(H, it == 0 ? G.bhr0[box] : G.bhrI[box], B->dtype == CFD_F32, st)) != CFD_OK)
+            return s;
         }
         P.halo_in = halo[(n_iter - 1) & 1];
         P.kext = E + 4;

@@ -40,16 +40,16 @@ def torch():
     return torch
 
 
-def run(lib, torch, B, buf, nf, prec, dtype=np.float64, mask=None):
+def run(lib, torch, B, buf, nf, prec, dtype=np.float64, mask=None, n_iter=0):
     mask = lib.CFD_OP_ALL if mask is None else mask
     dev = torch.device("cuda", 0)
     fields = torch.from_numpy(np.ascontiguousarray(buf.astype(dtype))).to(dev)
     nops = bin(mask).count("1")
     nint = sum(int(n) ** 3 for n in B.block_n)
     out = torch.full((nint * nf * nops,), 7.0, dtype=fields.dtype, device=dev)
-    ws = lib.cfd_apply_workspace(B, nf, mask, prec, 0)
+    ws = lib.cfd_apply_workspace(B, nf, mask, prec, n_iter)
     work = torch.empty(max(ws, 256), dtype=torch.uint8, device=dev)
-    lib.cfd_apply(B, fields, nf, mask, prec, 0, out, work)
+    lib.cfd_apply(B, fields, nf, mask, prec, n_iter, out, work)
     lib.cfd_sync_status(B)
     return out.cpu().numpy()
 
@@ -81,16 +81,18 @@ def test_zero_fields_give_exact_zeros(lib, torch, dtype):
         assert np.all(got == 0.0), prec
 
 
+@pytest.mark.parametrize("n_iter", [0, 1])
 @pytest.mark.parametrize("scale_exp", [-995, 995])
-def test_fields_at_the_ends_of_the_fp64_range(lib, torch, scale_exp):
-    """sin-sum fields scaled by 2^-995 (~1e-300) and 2^995 (~1e300): same relative accuracy."""
+def test_fields_at_the_ends_of_the_fp64_range(lib, torch, scale_exp, n_iter):
+    """sin-sum fields scaled by 2^-995 (~1e-300) and 2^995 (~1e300): same relative accuracy,
+    closed and iterated (the halo passes scale each pencil by its own power of two too)."""
     NM, N = 64, 32
     dx, (Z, Y, X) = grid(NM)
     f = W.sine_sum(W.rng(41), 8, 1, 12)
     fg = np.ldexp(f(X, Y, Z), scale_exp)
     mesh, exts, buf, B = setup(lib, NM, N, [fg])
-    got = run(lib, torch, B, buf, 1, lib.CFD_TC_BF16_EXACT).reshape(mesh.nblocks, 9, N, N, N)
-    ref = C.apply_uniform(exts[0], oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2"), (dx, dx, dx), N, 4, OPS, 0)
+    got = run(lib, torch, B, buf, 1, lib.CFD_TC_BF16_EXACT, n_iter=n_iter).reshape(mesh.nblocks, 9, N, N, N)
+    ref = C.apply_uniform(exts[0], oracle_sch("Q13_1_d1"), oracle_sch("Q13_1_d2"), (dx, dx, dx), N, 4, OPS, n_iter)
     for i, op in enumerate(OPS):
         want = ref[op].reshape(mesh.nblocks, N, N, N)
         assert np.all(np.isfinite(got[:, i])), op
