@@ -96,6 +96,26 @@ __device__ __forceinline__ void hr_acc(float &sh, float &sl, float ch, float cl,
 
 // The four rows applied to one pencil: element j of the pencil is load(j), j < E, then the
 // four halo columns hv; coefficients (h, l) per column from shared memory.
+// An FP32 value as a double, exactly, with integer instructions (zeros and the negligible
+// subnormal error words give zero).
+__device__ __forceinline__ double hr_f2d(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu)), (int)(u << 29));
+}
+
+// (sh + sl) * 2^U: one FP64 add, the scale as an exponent-field add (ldexp where the result
+// would leave the normal range).
+__device__ __forceinline__ double hr_result(float sh, float sl, int U) {
+  const double d = hr_f2d(sh) + hr_f2d(sl);
+  const int hi = __double2hiint(d), lo = __double2loint(d);
+  const int e = (hi >> 20) & 0x7FF;
+  if (e == 0) return d;
+  if (e + U >= 1 && e + U <= 2046) return __hiloint2double(hi + (U << 20), lo);
+  return ldexp(d, U);
+}
+
 template <typename TI, typename Load>
 __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4], bool with_halo,
                                         const float4 *ch4, const float4 *cl4, double *o) {
@@ -135,7 +155,7 @@ __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4],
     }
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) o[r] = ldexp((double)sh[r] + (double)sl[r], U);
+  for (int r = 0; r < 4; ++r) o[r] = hr_result(sh[r], sl[r], U);
 }
 
 // One thread per pencil, 128 threads per CTA.  Each warp first stages its 32 pencils in
