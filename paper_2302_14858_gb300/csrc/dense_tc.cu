@@ -422,7 +422,7 @@ __device__ __forceinline__ long long stride_of(int axis, long long s0, long long
 constexpr int kProdWarps = CFD_DENSE_PRODUCER_WARPS;  // multiple of 4
 constexpr int kProducers = kProdWarps * 32;          // warps 0 .. kProdWarps-1
 constexpr int kParts = kProducers / 128;             // threads per pencil
-constexpr int kEpilogue = 256;                       // the next 8 warps
+constexpr int kEpilogue = 256;                       // the next 8 warps: two per TMEM lane quadrant
 constexpr int kThreads = kProducers + kEpilogue;
 constexpr int kPassCols = 160;    // TMEM columns per pass buffer ((L + 1) * R <= 160)
 constexpr int kPassBufs = 3;
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
         if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1), WL)) { failed = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int RH = R / 2, r0 = ehalf * RH;
+        const int RH = R / 2, r0 = ehalf * RH;  // the two warps of a quadrant split the rows
         const int sg = r0 / P.seg_rows, i0 = r0 - sg * P.seg_rows;
         const int mode = P.seg_mode[ps][sg];
         const bool wf = (mode == 0 || mode == 3) && interior;
@@ -1045,19 +1045,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const int rlo = ps ? rlo1 : rlo0, rhi = ps ? rhi1 : rhi0;
         const bool safe = !(wf || ws) || (!bad && ebase + rlo >= kExLo && ebase + rhi <= kExHi);
         const bool vec = P.xvec != 0;
+        const int ng = RH / 8;  // row groups; the last one releases the pass buffer
         if (__all_sync(0xffffffffu, safe)) {
 #pragma unroll 1
-          for (int gq = RH == 16 ? 0 : 1; gq < 2; ++gq) {
-            const int o8 = gq ? RH - 8 : 0;
+          for (int gq = 0; gq < ng; ++gq) {
+            const int o8 = gq * 8;
             epilogue_rows<8, L + 1, TO, false, TFM>(taddr + o8, (uint32_t)R, ebase, bad, rexp + o8, fb, f_ax, sb, sstr,
-                                                    wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, vec, gx, gyp);
+                                                    wf, ws, i0 + o8, gq == ng - 1 ? t_empty(tb) : 0u, vec, gx, gyp);
           }
         } else {
 #pragma unroll 1
-          for (int gq = RH == 16 ? 0 : 1; gq < 2; ++gq) {
-            const int o8 = gq ? RH - 8 : 0;
+          for (int gq = 0; gq < ng; ++gq) {
+            const int o8 = gq * 8;
             epilogue_rows<8, L + 1, TO, true, TFM>(taddr + o8, (uint32_t)R, ebase, bad, rexp + o8, fb, f_ax, sb, sstr,
-                                                   wf, ws, i0 + o8, gq ? t_empty(tb) : 0u, vec, gx, gyp);
+                                                   wf, ws, i0 + o8, gq == ng - 1 ? t_empty(tb) : 0u, vec, gx, gyp);
           }
         }
       }
