@@ -530,6 +530,82 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
   }
 }
 
+// The common cases of the epilogue, without the per-output branches of epilogue_rows: 8 rows
+// from the exact levels, every output in the normal range, final outputs (FP64 or FP32) and,
+// with SC, the FP64 intermediate (and the face neighbours' ghost copies where sc_x / sc_y are
+// set).  VEC: 16-byte stores along a contiguous output axis.
+template <int LEV, typename TO, bool VEC, bool SC>
+__device__ __forceinline__ void epilogue_fast8(uint32_t taddr, uint32_t lev_stride, int ebase, const int *rowexp,
+                                               TO *fin_base, long long fin_stride, double *sc_base,
+                                               long long sc_stride, double *sc_x, double *sc_y, int i0,
+                                               uint32_t t_empty_addr) {
+  uint32_t acc[LEV][8];
+#pragma unroll
+  for (int k = 0; k < LEV; ++k)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(acc[k][0]), "=r"(acc[k][1]), "=r"(acc[k][2]), "=r"(acc[k][3]), "=r"(acc[k][4]),
+                   "=r"(acc[k][5]), "=r"(acc[k][6]), "=r"(acc[k][7])
+                 : "r"(taddr + (uint32_t)k * lev_stride));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+  if (t_empty_addr) {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t_empty_addr));
+  }
+  const int4 ra = *reinterpret_cast<const int4 *>(rowexp), rb = *reinterpret_cast<const int4 *>(rowexp + 4);
+  const int rx[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+  TO o[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ex = rx[c] + ebase;
+    double dv = 0.0;
+    if (sizeof(TO) == 8 || SC) {
+      // Y = sum_k a_k 2^(8 (LEV-1-k)) as a 64-bit integer, one conversion, the scale as an
+      // exponent-field add (Y = 0 gives 0)
+      long long Y;
+      if constexpr (LEV == 5) {
+        const int t1 = (int)(acc[0][c] * 256u + acc[1][c] - 257u * kAccBiasBits);
+        const int t2 = (int)(acc[2][c] * 256u + acc[3][c] - 257u * kAccBiasBits);
+        Y = (long long)t1 * 16777216ll + (long long)t2 * 256ll + (long long)(int)(acc[4][c] - kAccBiasBits);
+      } else {
+        Y = 0;
+#pragma unroll
+        for (int k = 0; k < LEV; ++k) Y = Y * 256ll + (long long)(int)(acc[k][c] - kAccBiasBits);
+      }
+      const double d = __ll2double_rn(Y);
+      const int hi = __double2hiint(d), lo = __double2loint(d);
+      dv = __hiloint2double(hi ? hi + (ex << 20) : 0, lo);
+    }
+    if constexpr (sizeof(TO) == 8) {
+      o[c] = dv;
+    } else {
+      // FP32 outputs: the levels as exact floats, Horner in FP32, one power-of-two scale
+      float y = __uint_as_float(acc[0][c]) - kAccBias;
+#pragma unroll
+      for (int k = 1; k < LEV; ++k) y = fmaf(y, 256.0f, __uint_as_float(acc[k][c]) - kAccBias);
+      o[c] = y * __int_as_float((ex + 127) << 23);
+    }
+    if constexpr (SC) {
+      const long long i = i0 + c;
+      sc_base[i * sc_stride] = dv;
+      if (sc_x) sc_x[i * sc_stride] = dv;  // the face neighbour's ghost column
+      if (sc_y) sc_y[i * sc_stride] = dv;
+    }
+  }
+  if constexpr (VEC) {
+    if constexpr (sizeof(TO) == 8) {
+#pragma unroll
+      for (int c = 0; c < 8; c += 2) *reinterpret_cast<double2 *>(fin_base + i0 + c) = make_double2(o[c], o[c + 1]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; c += 4)
+        *reinterpret_cast<float4 *>(fin_base + i0 + c) = make_float4(o[c], o[c + 1], o[c + 2], o[c + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) fin_base[(long long)(i0 + c) * fin_stride] = o[c];
+  }
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count));
 }
@@ -1046,7 +1122,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const bool safe = !(wf || ws) || (!bad && ebase + rlo >= kExLo && ebase + rhi <= kExHi);
         const bool vec = P.xvec != 0;
         const int ng = RH / 8;  // row groups; the last one releases the pass buffer
-        if (__all_sync(0xffffffffu, safe)) {
+        // the common cases first: final outputs, with or without the intermediate (warp-uniform
+        // choices: tcgen05.ld is a warp-wide instruction)
+        const bool fast = !TFM && safe && wf;
+        if (__all_sync(0xffffffffu, fast && !ws)) {
+#pragma unroll 1
+          for (int gq = 0; gq < ng; ++gq) {
+            const int o8 = gq * 8;
+            const uint32_t rel = gq == ng - 1 ? t_empty(tb) : 0u;
+            if (vec)
+              epilogue_fast8<L + 1, TO, true, false>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, nullptr, 0,
+                                                    nullptr, nullptr, i0 + o8, rel);
+            else
+              epilogue_fast8<L + 1, TO, false, false>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, nullptr, 0,
+                                                     nullptr, nullptr, i0 + o8, rel);
+          }
+        } else if (sizeof(TO) == 8 && __all_sync(0xffffffffu, fast && ws)) {
+#pragma unroll 1
+          for (int gq = 0; gq < ng; ++gq) {
+            const int o8 = gq * 8;
+            const uint32_t rel = gq == ng - 1 ? t_empty(tb) : 0u;
+            if (vec)
+              epilogue_fast8<L + 1, TO, true, true>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, sb, sstr, gx,
+                                                   gyp, i0 + o8, rel);
+            else
+              epilogue_fast8<L + 1, TO, false, true>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, sb, sstr, gx,
+                                                    gyp, i0 + o8, rel);
+          }
+        } else if (__all_sync(0xffffffffu, safe)) {
 #pragma unroll 1
           for (int gq = 0; gq < ng; ++gq) {
             const int o8 = gq * 8;
