@@ -55,6 +55,7 @@ struct DenseParams {
   CUtensorMap tmap;          // (the type carries its own 128-byte alignment)
   int *status;
   long long wait_limit;      // clock cycles a main-loop wait may take before it latches CFD_ERR_TIMEOUT
+  float inv_tpj, inv_nf, inv_n2;  // 1 / tiles_per_job, 1 / nf, 1 / n2 (set at launch)
 };
 
 // The four operator rows of one halo pass of the hybrid iteration (Eq. iter_center_P: rows 1

@@ -654,20 +654,24 @@ __device__ __forceinline__ int dir_index_dev(int dz, int dy, int dx) {
 }
 
 // pencil index p (within the block and field) of pencil `pencil` of a tile
+// n / d for 0 <= n < 2^22 with inv = 1/d rounded to FP32: (n + 1/2) / d stays at least 1/(2d)
+// away from an integer, more than the two roundings can move it
+__device__ __forceinline__ int fdiv(int n, float inv) { return __float2int_rz(((float)n + 0.5f) * inv); }
+
 __device__ __forceinline__ int tile_pencil(const DenseParams &P, int tile, int pencil) {
-  const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
+  const int job = fdiv(tile, P.inv_tpj), tj = tile - job * P.tiles_per_job;
   return tj * kTile + pencil;
 }
 
 __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, int pencil) {
   TileCoord c;
-  const int job = tile / P.tiles_per_job, tj = tile - job * P.tiles_per_job;
-  c.lb = job / P.nf;
+  const int job = fdiv(tile, P.inv_tpj), tj = tile - job * P.tiles_per_job;
+  c.lb = fdiv(job, P.inv_nf);
   c.q = job - c.lb * P.nf;
   c.b = P.contig ? P.b0 + c.lb : P.blocks[c.lb];
   const int p = tj * kTile + pencil;
   c.valid = p < P.n1 * P.n2;
-  c.t1 = c.valid ? p / P.n2 : 0;
+  c.t1 = c.valid ? fdiv(p, P.inv_n2) : 0;
   c.t2 = c.valid ? p - c.t1 * P.n2 : 0;
   return c;
 }
@@ -910,12 +914,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       }
       TI v[CPP][8];
       int em = 0;
+      const int kv = c.valid ? P.kext : 0;  // values of this pencil (none for a pencil past the end)
 #pragma unroll
       for (int h = 0; h < CPP; ++h) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int j = (half + kParts * h) * 8 + k;
-          v[h][k] = (j < P.kext && c.valid) ? stg[stg_index(j)] : TI(0);
+          v[h][k] = j < kv ? stg[stg_index(j)] : TI(0);
           em = max(em, biased_exp(v[h][k]));
         }
       }
@@ -936,7 +941,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       // A[buf] must be free: the MMAs of its previous use have completed
       if (use > 0 && !mbar_wait_bounded(a_empty(buf), (uint32_t)((use - 1) & 1), WL)) failed = true;
       if (half == 0) s_etau[(it & 7) * kTile + pl] = bad_pencil ? kBadTau : tau_exp(emax, TI(0));
-      if (bad_pencil) emax = 0;
+      // a non-finite pencil: every shift in fixed_of / tf32_of runs past the significand (zero digits)
+      if (bad_pencil) emax = nonfinite_exp(TI(0)) + 128;
       uint16_t *Ab = sA + (size_t)buf * (A_BYTES / 2);
       const int row_group = pl >> 3, row_in = pl & 7;
       if constexpr (TFM) {
@@ -948,7 +954,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
           if (ch >= NCH) break;
           uint32_t w[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) w[k] = (emax && ch * 8 < P.kext) ? tf32_of(v[h][k], emax) : 0u;
+          for (int k = 0; k < 8; ++k) w[k] = ch * 8 < P.kext ? tf32_of(v[h][k], emax) : 0u;
 #pragma unroll
           for (int q = 0; q < 2; ++q)
             *reinterpret_cast<uint4 *>(A32 + ((size_t)row_group * (KP / 4) + 2 * ch + q) * 32 + row_in * 4) =
@@ -972,8 +978,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
           uint32_t d0[S], d1[S];
-          digits_of<S>(emax ? fixed_of(v[h][k], emax) : 0ll, d0);
-          digits_of<S>(emax ? fixed_of(v[h][k + 1], emax) : 0ll, d1);
+          digits_of<S>(fixed_of(v[h][k], emax), d0);
+          digits_of<S>(fixed_of(v[h][k + 1], emax), d1);
 #pragma unroll
           for (int t = 0; t < S; ++t) w[t][k / 2] = __byte_perm(d0[t], d1[t], 0x7632);
         }
@@ -1199,6 +1205,9 @@ cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned g
   launch_begin(KF_DENSE, st);
   DenseParams Q = P;
   Q.wait_limit = dense_wait_limit();
+  Q.inv_tpj = 1.0f / (float)Q.tiles_per_job;
+  Q.inv_nf = 1.0f / (float)Q.nf;
+  Q.inv_n2 = 1.0f / (float)Q.n2;
   fn<<<grid, kThreads, smem, st>>>(Q);
   launch_end(KF_DENSE, st);
   return cuda_fail(cudaGetLastError(), "k_dense launch");
