@@ -94,8 +94,6 @@ __device__ __forceinline__ void hr_acc(float &sh, float &sl, float ch, float cl,
   sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(er, pe), cross));
 }
 
-// The four rows applied to one pencil: element j of the pencil is load(j), j < E, then the
-// four halo columns hv; coefficients (h, l) per column from shared memory.
 // An FP32 value as a double, exactly, with integer instructions (zeros and the negligible
 // subnormal error words give zero).
 __device__ __forceinline__ double hr_f2d(float x) {
@@ -116,6 +114,8 @@ __device__ __forceinline__ double hr_result(float sh, float sl, int U) {
   return ldexp(d, U);
 }
 
+// The four rows applied to one pencil: element j of the pencil is load(j), j < E, then the
+// four halo columns hv; coefficients (h, l) per column from shared memory.
 template <typename TI, typename Load>
 __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4], bool with_halo,
                                         const float4 *ch4, const float4 *cl4, double *o) {
