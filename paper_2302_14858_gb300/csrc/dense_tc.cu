@@ -534,7 +534,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, uint32_t lev_strid
 // from the exact levels, every output in the normal range, final outputs (FP64 or FP32) and,
 // with SC, the FP64 intermediate (and the face neighbours' ghost copies where sc_x / sc_y are
 // set).  VEC: 16-byte stores along a contiguous output axis.
-template <int LEV, typename TO, bool VEC, bool SC>
+template <int LEV, typename TO, bool VEC, bool SC, int TFM>
 __device__ __forceinline__ void epilogue_fast8(uint32_t taddr, uint32_t lev_stride, int ebase, const int *rowexp,
                                                TO *fin_base, long long fin_stride, double *sc_base,
                                                long long sc_stride, double *sc_x, double *sc_y, int i0,
@@ -558,7 +558,23 @@ __device__ __forceinline__ void epilogue_fast8(uint32_t taddr, uint32_t lev_stri
   for (int c = 0; c < 8; ++c) {
     const int ex = rx[c] + ebase;
     double dv = 0.0;
-    if (sizeof(TO) == 8 || SC) {
+    if constexpr (TFM) {
+      // TF32 form: one FP32 accumulator a per output; a * 2^ex as FP64 from its bits (zero gives
+      // zero; an FP32 subnormal, which the exact products cannot produce above 2^-126 of the
+      // scale, takes the library conversion)
+      const uint32_t u = acc[0][c];
+      const float a = __uint_as_float(u);
+      const int ef = (int)((u >> 23) & 0xFFu);
+      if (sizeof(TO) == 8 || SC) {
+        if (ef)
+          dv = __hiloint2double((int)((u & 0x80000000u) | ((uint32_t)(ef + 896 + ex) << 20) | ((u >> 3) & 0xFFFFFu)),
+                                (int)(u << 29));
+        else
+          dv = (u & 0x7FFFFFFFu) ? ldexp((double)a, ex) : __hiloint2double((int)(u & 0x80000000u), 0);
+      }
+      if constexpr (sizeof(TO) == 8) o[c] = dv;
+      else o[c] = a * __int_as_float((ex + 127) << 23);
+    } else if (sizeof(TO) == 8 || SC) {
       // Y = sum_k a_k 2^(8 (LEV-1-k)) as a 64-bit integer, one conversion, the scale as an
       // exponent-field add (Y = 0 gives 0)
       long long Y;
@@ -575,7 +591,8 @@ __device__ __forceinline__ void epilogue_fast8(uint32_t taddr, uint32_t lev_stri
       const int hi = __double2hiint(d), lo = __double2loint(d);
       dv = __hiloint2double(hi ? hi + (ex << 20) : 0, lo);
     }
-    if constexpr (sizeof(TO) == 8) {
+    if constexpr (TFM) {
+    } else if constexpr (sizeof(TO) == 8) {
       o[c] = dv;
     } else {
       // FP32 outputs: the levels as exact floats, Horner in FP32, one power-of-two scale
@@ -1130,17 +1147,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         const int ng = RH / 8;  // row groups; the last one releases the pass buffer
         // the common cases first: final outputs, with or without the intermediate (warp-uniform
         // choices: tcgen05.ld is a warp-wide instruction)
-        const bool fast = !TFM && safe && wf;
+        const bool fast = safe && wf;
         if (__all_sync(0xffffffffu, fast && !ws)) {
 #pragma unroll 1
           for (int gq = 0; gq < ng; ++gq) {
             const int o8 = gq * 8;
             const uint32_t rel = gq == ng - 1 ? t_empty(tb) : 0u;
             if (vec)
-              epilogue_fast8<L + 1, TO, true, false>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, nullptr, 0,
+              epilogue_fast8<L + 1, TO, true, false, TFM>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, nullptr, 0,
                                                     nullptr, nullptr, i0 + o8, rel);
             else
-              epilogue_fast8<L + 1, TO, false, false>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, nullptr, 0,
+              epilogue_fast8<L + 1, TO, false, false, TFM>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, nullptr, 0,
                                                      nullptr, nullptr, i0 + o8, rel);
           }
         } else if (sizeof(TO) == 8 && __all_sync(0xffffffffu, fast && ws)) {
@@ -1149,10 +1166,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
             const int o8 = gq * 8;
             const uint32_t rel = gq == ng - 1 ? t_empty(tb) : 0u;
             if (vec)
-              epilogue_fast8<L + 1, TO, true, true>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, sb, sstr, gx,
+              epilogue_fast8<L + 1, TO, true, true, TFM>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, sb, sstr, gx,
                                                    gyp, i0 + o8, rel);
             else
-              epilogue_fast8<L + 1, TO, false, true>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, sb, sstr, gx,
+              epilogue_fast8<L + 1, TO, false, true, TFM>(taddr + o8, (uint32_t)R, ebase, rexp + o8, fb, f_ax, sb, sstr, gx,
                                                     gyp, i0 + o8, rel);
           }
         } else if (__all_sync(0xffffffffu, safe)) {
