@@ -52,6 +52,9 @@ struct DenseParams {
   // nl: [nblk][4] local indices of the x-, x+, y-, y+ face neighbours.
   int ghost_x, ghost_y;
   const int *nl;
+  // Scratch block index of each block of the launch (null: its position in blocks): a strip
+  // launch over some blocks of a group writes into the group's intermediate boxes.
+  const int *sc_local;
   CUtensorMap tmap;          // (the type carries its own 128-byte alignment)
   int *status;
   long long wait_limit;      // clock cycles a main-loop wait may take before it latches CFD_ERR_TIMEOUT

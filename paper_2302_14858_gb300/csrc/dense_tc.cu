@@ -1119,7 +1119,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
                 ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
                 (long long)(c.t1 - P.int_lo1) * f_t1 + (long long)(c.t2 - P.int_lo2) * f_t2;
         if (ws)
-          sb += ((long long)c.lb * P.nf + c.q) * (long long)P.sc_box + (long long)(sc_s1 + c.t1) * c_t1 +
+          sb += ((long long)(P.sc_local ? P.sc_local[c.lb] : c.lb) * P.nf + c.q) * (long long)P.sc_box +
+                (long long)(sc_s1 + c.t1) * c_t1 +
                 (long long)(sc_s2 + c.t2) * c_t2;
         const long long sstr = c_ax;
         // interior pencils near an x (y) face also fill the neighbour's ghost column (row)
@@ -1127,12 +1128,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
         if (ws && P.ghost_x) {
           const int xs = sc_s2 + c.t2;  // t2 is the x axis in the stages that write intermediates
           const long long jump = (long long)P.nf * (long long)P.sc_box;
-          if (xs < 2 * g) gx = sb + (long long)(P.nl[c.lb * 4 + 0] - c.lb) * jump + N;
-          else if (xs >= N) gx = sb + (long long)(P.nl[c.lb * 4 + 1] - c.lb) * jump - N;
+          // (no write where the block has no such neighbour: it computes that strip itself)
+          const int *nl = P.nl + c.lb * 4;
+          if (xs < 2 * g) { if (nl[0] >= 0) gx = sb + (long long)(nl[0] - c.lb) * jump + N; }
+          else if (xs >= N) { if (nl[1] >= 0) gx = sb + (long long)(nl[1] - c.lb) * jump - N; }
           if (P.ghost_y) {
             const int ys = sc_s1 + c.t1;  // t1 is the y axis (z stage)
-            if (ys < 2 * g) gyp = sb + (long long)(P.nl[c.lb * 4 + 2] - c.lb) * jump + (long long)N * ss1;
-            else if (ys >= N) gyp = sb + (long long)(P.nl[c.lb * 4 + 3] - c.lb) * jump - (long long)N * ss1;
+            if (ys < 2 * g) { if (nl[2] >= 0) gyp = sb + (long long)(nl[2] - c.lb) * jump + (long long)N * ss1; }
+            else if (ys >= N) { if (nl[3] >= 0) gyp = sb + (long long)(nl[3] - c.lb) * jump - (long long)N * ss1; }
           }
         }
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
@@ -1258,8 +1261,13 @@ struct DenseGroup {
   // rows 1 and N-2 per degree of [0]D and of the iterated operator (unscaled), for the halo
   // passes on the CUDA cores
   HaloRows hr0[3], hrI[3];
-  bool faces_x = false, faces_y = false;  // every block has both x (y) face neighbours
-  int *d_nl = nullptr;   // device [nblk][4]: local indices of the x-, x+, y-, y+ neighbours
+  int *d_nl = nullptr;   // device [nblk][4]: local indices of the x-, x+, y-, y+ neighbours (-1: none)
+  // blocks of the group without a same-size, reciprocal face neighbour on side x-, x+, y-, y+:
+  // global ids and local indices (device), for the strips of intermediates they compute
+  // themselves (their neighbours cannot write those ghost columns)
+  int nmiss[4] = {0, 0, 0, 0};
+  int *d_miss_b[4] = {nullptr, nullptr, nullptr, nullptr};
+  int *d_miss_l[4] = {nullptr, nullptr, nullptr, nullptr};
   // biased first-degree operators ([box][0 left-biased S+, 1 right-biased S-]), dx-scaled:
   // closed (or cyclic) [0]D, iterated [D1 | coupling in halo column E (S+) or E+3 (S-)];
   // halo images (unscaled): row 1 = S+ row N-kc, row 2 = S- row kc-1
@@ -1410,43 +1418,51 @@ cfd_status dense_bind(cfd_blocks_s *B) {
         G.biased = true;
       }
     }
-    {
-      auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
-      G.faces_x = G.faces_y = true;
-      // both face neighbours present and reciprocal (the neighbour's opposite face is this block)
-      auto face = [&](int b, int dy, int dx) {
-        const int nb = B->nbr[b * 26 + di(0, dy, dx)];
-        return nb >= 0 && B->nbr[nb * 26 + di(0, -dy, -dx)] == b;
-      };
-      for (int b : B->groups[gi]) {
-        if (!face(b, 0, -1) || !face(b, 0, 1)) G.faces_x = false;
-        if (!face(b, -1, 0) || !face(b, 1, 0)) G.faces_y = false;
-      }
-    }
     st->groups.push_back(G);
   }
-  std::vector<int> lidx(B->nblocks, 0);
+  std::vector<int> lidx(B->nblocks, 0), gidx(B->nblocks, -1);
   for (size_t gi = 0; gi < B->groups.size(); ++gi)
-    for (size_t k = 0; k < B->groups[gi].size(); ++k) lidx[B->groups[gi][k]] = (int)k;
+    for (size_t k = 0; k < B->groups[gi].size(); ++k) {
+      lidx[B->groups[gi][k]] = (int)k;
+      gidx[B->groups[gi][k]] = (int)gi;
+    }
   for (size_t gi = 0; gi < B->groups.size(); ++gi) {
     DenseGroup &G = st->groups[gi];
-    if (!G.faces_x) continue;
+    if (!G.ok) continue;
     auto di = [](int dz, int dy, int dx) { int r = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1); return r > 13 ? r - 1 : r; };
     const std::vector<int> &gb = B->groups[gi];
+    // per block and side: the local index of a same-group, reciprocal face neighbour, or -1
+    const int sdy[4] = {0, 0, -1, 1}, sdx[4] = {-1, 1, 0, 0};
     std::vector<int> nl(gb.size() * 4, -1);
+    std::vector<int> mb[4], ml[4];
     for (size_t k = 0; k < gb.size(); ++k) {
       const int b = gb[k];
-      const int nx0 = B->nbr[b * 26 + di(0, 0, -1)], nx1 = B->nbr[b * 26 + di(0, 0, 1)];
-      nl[k * 4 + 0] = lidx[nx0];
-      nl[k * 4 + 1] = lidx[nx1];
-      if (G.faces_y) {
-        nl[k * 4 + 2] = lidx[B->nbr[b * 26 + di(0, -1, 0)]];
-        nl[k * 4 + 3] = lidx[B->nbr[b * 26 + di(0, 1, 0)]];
+      for (int sd = 0; sd < 4; ++sd) {
+        const int nb = B->nbr[b * 26 + di(0, sdy[sd], sdx[sd])];
+        const bool ok = nb >= 0 && gidx[nb] == (int)gi && B->nbr[nb * 26 + di(0, -sdy[sd], -sdx[sd])] == b;
+        if (ok) {
+          nl[k * 4 + sd] = lidx[nb];
+        } else {
+          mb[sd].push_back(b);
+          ml[sd].push_back((int)k);
+        }
       }
     }
     cfd_status s = cuda_fail(cudaMalloc((void **)&G.d_nl, nl.size() * 4), "cudaMalloc");
     if (G.d_nl) B->d_dense_ptrs.push_back(G.d_nl);
     if (s == CFD_OK) s = cuda_fail(cudaMemcpy(G.d_nl, nl.data(), nl.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    for (int sd = 0; sd < 4 && s == CFD_OK; ++sd) {
+      G.nmiss[sd] = (int)mb[sd].size();
+      if (mb[sd].empty()) continue;
+      s = cuda_fail(cudaMalloc((void **)&G.d_miss_b[sd], mb[sd].size() * 4), "cudaMalloc");
+      if (G.d_miss_b[sd]) B->d_dense_ptrs.push_back(G.d_miss_b[sd]);
+      if (s == CFD_OK) s = cuda_fail(cudaMalloc((void **)&G.d_miss_l[sd], ml[sd].size() * 4), "cudaMalloc");
+      if (G.d_miss_l[sd]) B->d_dense_ptrs.push_back(G.d_miss_l[sd]);
+      if (s == CFD_OK)
+        s = cuda_fail(cudaMemcpy(G.d_miss_b[sd], mb[sd].data(), mb[sd].size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+      if (s == CFD_OK)
+        s = cuda_fail(cudaMemcpy(G.d_miss_l[sd], ml[sd].data(), ml[sd].size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
     if (s != CFD_OK) return s;
   }
   return CFD_OK;
@@ -1786,13 +1802,35 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       set_segments(P, 2, odx >= 0 ? 0 : -1, odx, odxx >= 0 ? 0 : -1, odxx);
       if ((s = run_stage(P, 2)) != CFD_OK) return s;
     }
-    // S_y: D_y on (z interior, x extended if d_xy) -> d_y, d_yy, and G_y = D_y f for d_xy
-    // With face neighbours along x (and y), the intermediates are computed on the interior
-    // pencils only; the epilogue also writes each value within g of a face into the face
-    // neighbour's ghost column (row), which is what local evaluation there would give.
+    // Intermediates for the mixed derivatives: G_y = D_y f on the x-extended (z, x) pencils,
+    // G_z = D_z f on the x- and y-extended (y, x) pencils (not the corners).  Each block
+    // computes its interior pencils; the epilogue also writes each value within g of an x (y)
+    // face into the face neighbour's ghost column (row), which is what local evaluation there
+    // would give (same input data, same arithmetic).  A block without a same-size face
+    // neighbour on a side computes that strip of ghost pencils itself, in a small launch over
+    // the blocks missing that side.  (Blocks narrower than 2g take the extended pencils
+    // directly.)
+    auto strip = [&](DenseParams P, int sd, int lo1, int n1, int lo2, int n2) -> cfd_status {
+      if (G.nmiss[sd] == 0) return CFD_OK;
+      P.blocks = G.d_miss_b[sd];
+      P.sc_local = G.d_miss_l[sd];
+      P.nblk = G.nmiss[sd];
+      P.contig = 0;
+      P.in_start[P.t1] = lo1;
+      P.in_start[P.t2] = lo2;
+      P.n1 = n1;
+      P.n2 = n2;
+      P.sc_start[P.t2] = lo2;              // the x axis: scratch and input coordinates agree
+      if (P.t1 == 1) P.sc_start[1] = lo1;  // the y axis of G_z likewise (z of G_y is interior only)
+      P.ghost_x = P.ghost_y = 0;
+      P.int_lo1 = P.int_hi1 = P.int_lo2 = P.int_hi2 = 0;
+      set_segments(P, P.axis, 2, 0, -1, -1);  // the degree-1 operator, intermediate only
+      return run(P);
+    };
+    // S_y: D_y on (z interior, x interior) -> d_y, d_yy, and G_y for d_xy
     if (ody >= 0 || odyy >= 0 || odxy >= 0) {
       const bool ext = odxy >= 0;
-      const bool copy = ext && G.faces_x && N >= 2 * g;  // interior pencils + ghost columns from the epilogue
+      const bool copy = ext && N >= 2 * g;  // interior pencils + ghost columns from the epilogue
       DenseParams P = field_stage(1, 0, 2, g, N, (ext && !copy) ? 0 : g, (ext && !copy) ? E : N);
       const int m1 = (ody >= 0 && ext) ? 3 : (ody >= 0 ? 0 : (ext ? 2 : -1));
       set_segments(P, 1, m1, ody, odyy >= 0 ? 0 : -1, odyy);
@@ -1805,11 +1843,15 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.nl = G.d_nl;
       }
       if ((s = run_stage(P, 1)) != CFD_OK) return s;
+      if (copy) {
+        if ((s = strip(P, 0, g, N, 0, g)) != CFD_OK) return s;          // x- ghost columns
+        if ((s = strip(P, 1, g, N, N + g, g)) != CFD_OK) return s;      // x+
+      }
     }
-    // S_z: D_z on (y, x) extended for d_xz / d_yz -> d_z, d_zz, and G_z = D_z f
+    // S_z: D_z on (y, x) interior -> d_z, d_zz, and G_z for d_xz / d_yz
     if (odz >= 0 || odzz >= 0 || odxz >= 0 || odyz >= 0) {
       const bool ext = odxz >= 0 || odyz >= 0;
-      const bool copy = ext && G.faces_x && G.faces_y && N >= 2 * g;
+      const bool copy = ext && N >= 2 * g;
       const bool wide = ext && !copy;
       DenseParams P = field_stage(0, 1, 2, wide ? 0 : g, wide ? E : N, wide ? 0 : g, wide ? E : N);
       const int m1 = (odz >= 0 && ext) ? 3 : (odz >= 0 ? 0 : (ext ? 2 : -1));
@@ -1823,7 +1865,12 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
         P.nl = G.d_nl;
       }
       if ((s = run_stage(P, 0)) != CFD_OK) return s;
-
+      if (copy) {
+        if ((s = strip(P, 0, g, N, 0, g)) != CFD_OK) return s;          // x- ghost columns
+        if ((s = strip(P, 1, g, N, N + g, g)) != CFD_OK) return s;      // x+
+        if ((s = strip(P, 2, 0, g, g, N)) != CFD_OK) return s;          // y- ghost rows
+        if ((s = strip(P, 3, N + g, g, g, N)) != CFD_OK) return s;      // y+
+      }
     }
     // T stages on the intermediates (one order of the mixed product: the closed
     // block operators of two axes commute, D_i D_j = D_j D_i)
