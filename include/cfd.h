@@ -69,6 +69,10 @@ typedef enum cfd_status {
  *     same pencils);
  *   - outputs that overflow become infinities; FP64 outputs below the normal
  *     range flush to zero, FP32 outputs round as IEEE.
+ * With n_iter > 0 the values the neighbours read at their k^c nodes (the halo
+ * rows of each iterate) are computed on the CUDA cores in compensated FP32
+ * (~2^-46 of sum_j |c_j f_j|), then enter the final pass as four extra inputs of
+ * each pencil in the format above.
  */
 typedef enum cfd_precision {
   CFD_FP64_BANDED = 0,   /* FP64 right-hand side + Thomas solve per pencil */
@@ -482,7 +486,8 @@ const char *cfd_last_error(void);
 /*
  * Diagnostics (no counterpart in the paper).  Kernel families:
  * 0 ghost exchange, 1 banded line solve, 2 RK4 combine, 3 dense tensor-core
- * operator, 4 dense halo rows, 5 biased line solve (cfd_apply_biased,
+ * operator, 4 halo rows of the hybrid iteration on the tensor-core path
+ * (CUDA cores), 5 biased line solve (cfd_apply_biased,
  * cfd_advect).  cfd_kernel_launches() counts every kernel the
  * library has launched in this process.  With profiling on, every launch is
  * bracketed by CUDA events recorded on its own stream; cfd_profile_read()
