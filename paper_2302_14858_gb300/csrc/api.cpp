@@ -460,6 +460,7 @@ void cfd_blocks_destroy(cfd_blocks_t B) {
   cudaSetDevice(B->device);
   cudaFree(B->d_nbr);
   cudaFree(B->d_extpre);
+  cudaFree(B->d_exch);
   cudaFree(B->d_intpre);
   cudaFree(B->d_scale);
   cudaFree(B->d_nvec);
@@ -568,6 +569,21 @@ cfd_status cfd_blocks_bind(cfd_scheme_t scheme, int nblocks, const int *block_n,
     int *p = nullptr;
     if ((s = upload(&p, grp.data(), grp.size())) != CFD_OK) return fail(s, nullptr);
     B->d_groups.push_back(p);
+    bool consecutive = true;
+    for (size_t k = 0; k < grp.size(); ++k)
+      if (grp[k] != grp[0] + (int)k) consecutive = false;
+    B->group_b0.push_back(consecutive ? grp[0] : -1);
+  }
+  {
+    std::vector<long long> exch((size_t)nblocks * 27);
+    for (int b = 0; b < nblocks; ++b) {
+      for (int d = 0; d < 26; ++d) {
+        const int nb = B->nbr[(size_t)b * 26 + d];
+        exch[(size_t)b * 27 + d] = nb >= 0 ? B->extpre[nb] : -1;
+      }
+      exch[(size_t)b * 27 + 26] = B->extpre[b];
+    }
+    if ((s = upload(&B->d_exch, exch.data(), exch.size())) != CFD_OK) return fail(s, nullptr);
   }
   if ((s = cuda_fail(cudaMalloc((void **)&B->d_status, sizeof(int)), "cudaMalloc")) != CFD_OK) return fail(s, nullptr);
   if ((s = cuda_fail(cudaMemset(B->d_status, 0, sizeof(int)), "cudaMemset")) != CFD_OK) return fail(s, nullptr);

@@ -27,55 +27,72 @@ template <typename T, int V> struct VecOf { using type = T; };
 template <> struct VecOf<double, 2> { using type = double2; };
 template <> struct VecOf<float, 4> { using type = float4; };
 
-// One thread per V consecutive ghost cells along x (V values = 16 bytes where the
-// ghost width, N and the rows keep 16-byte alignment; V = 1 otherwise), enumerated
-// without idle threads: part A covers the rows (fixed z, y) that lie in the ghost
-// shell along y or z (all of x), part B the x ghosts of the N^2 interior rows.
-// Consecutive threads take consecutive x, so destination rows and source segments
-// are contiguous.  The common (N, g) pairs are compiled with constant sizes
-// (divisions become multiply-shifts); NC = 0 takes them at run time.
+// One thread per kVPT groups of V consecutive ghost cells along x (V values = 16 bytes where
+// the ghost width, N and the rows keep 16-byte alignment; V = 1 otherwise), enumerated without
+// idle threads: part A covers the rows (fixed z, y) that lie in the ghost shell along y or z
+// (all of x), part B the x ghosts of the N^2 interior rows.  Consecutive threads take
+// consecutive x, so destination rows and source segments are contiguous.  The field offsets
+// of the block and its 26 neighbours come from one table (one load each, independent of the
+// data), and each thread issues its kVPT copies together, so the copies, not a chain of
+// dependent table loads, set the pace.  The common (N, g) pairs are compiled with constant
+// sizes (divisions become multiply-shifts); NC = 0 takes them at run time.
+constexpr int kVPT = 4;
+
 template <typename T, int NC, int GC, int V>
-__global__ void k_exchange(T *f, int nf, const int *__restrict__ blocks, int N_, int g_,
-                           const long long *__restrict__ extpre, const int *__restrict__ nbr) {
+__global__ void __launch_bounds__(256) k_exchange(T *f, int nf, const int *__restrict__ blocks, int b0, int N_,
+                                                  int g_, const long long *__restrict__ tab) {
   using VT = typename VecOf<T, V>::type;
   const int N = NC ? NC : N_, g = NC ? GC : g_;
   const int E = N + 2 * g, Ev = E / V, gv = g / V, Nv = N / V, G2v = 2 * gv;
   const int nA = (E * E - N * N) * Ev, nB = N * N * G2v;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nA + nB) return;
-  int x, y, z;
-  if (idx < nA) {
-    const int r = idx / Ev;
-    x = (idx - r * Ev) * V;
-    const int G2 = 2 * g;
-    if (r < G2 * E) {              // z in the ghost shell: whole planes
-      const int zz = r / E;
-      y = r - zz * E;
-      z = zz < g ? zz : zz + N;
-    } else {                       // z interior, y in the ghost shell
-      const int r2 = r - G2 * E, zz = r2 / G2, yy = r2 - zz * G2;
-      z = g + zz;
-      y = yy < g ? yy : yy + N;
-    }
-  } else {                         // interior row, x ghosts
-    const int r = idx - nA, row = r / G2v, xx = r - row * G2v, zz = row / N;
-    x = (xx < gv ? xx : xx + Nv) * V;
-    y = g + row - zz * N;
-    z = g + zz;
-  }
   const int job = blockIdx.y;
   const int lb = job / nf, q = job - lb * nf;
-  const int b = blocks[lb];
-  const int dx = x < g ? -1 : (x >= N + g ? 1 : 0);
-  const int dy = y < g ? -1 : (y >= N + g ? 1 : 0);
-  const int dz = z < g ? -1 : (z >= N + g ? 1 : 0);
-  const int nb = nbr[b * 26 + dir_index(dz, dy, dx)];
-  if (nb < 0) return;
-  const int cells = E * E * E;
-  const int dst = (z * E + y) * E + x;
-  const int src = dst - ((dz * E + dy) * E + dx) * N;
-  *reinterpret_cast<VT *>(f + nf * extpre[b] + (long long)(q * cells + dst)) =
-      *reinterpret_cast<const VT *>(f + nf * extpre[nb] + (long long)(q * cells + src));
+  const int b = b0 >= 0 ? b0 + lb : blocks[lb];
+  const long long *tb = tab + (long long)b * 27;
+  const long long cells = (long long)E * E * E;
+  T *base = f + nf * tb[26] + q * cells;
+  int dst[kVPT], src[kVPT];
+  long long nbo[kVPT];
+#pragma unroll
+  for (int u = 0; u < kVPT; ++u) {
+    const int idx = (blockIdx.x * kVPT + u) * blockDim.x + threadIdx.x;
+    nbo[u] = -1;
+    dst[u] = src[u] = 0;
+    if (idx >= nA + nB) continue;
+    int x, y, z;
+    if (idx < nA) {
+      const int r = idx / Ev;
+      x = (idx - r * Ev) * V;
+      const int G2 = 2 * g;
+      if (r < G2 * E) {              // z in the ghost shell: whole planes
+        const int zz = r / E;
+        y = r - zz * E;
+        z = zz < g ? zz : zz + N;
+      } else {                       // z interior, y in the ghost shell
+        const int r2 = r - G2 * E, zz = r2 / G2, yy = r2 - zz * G2;
+        z = g + zz;
+        y = yy < g ? yy : yy + N;
+      }
+    } else {                         // interior row, x ghosts
+      const int r = idx - nA, row = r / G2v, xx = r - row * G2v, zz = row / N;
+      x = (xx < gv ? xx : xx + Nv) * V;
+      y = g + row - zz * N;
+      z = g + zz;
+    }
+    const int dx = x < g ? -1 : (x >= N + g ? 1 : 0);
+    const int dy = y < g ? -1 : (y >= N + g ? 1 : 0);
+    const int dz = z < g ? -1 : (z >= N + g ? 1 : 0);
+    nbo[u] = __ldg(tb + dir_index(dz, dy, dx));
+    dst[u] = (z * E + y) * E + x;
+    src[u] = dst[u] - ((dz * E + dy) * E + dx) * N;
+  }
+  VT v[kVPT];
+#pragma unroll
+  for (int u = 0; u < kVPT; ++u)
+    if (nbo[u] >= 0) v[u] = *reinterpret_cast<const VT *>(f + nf * nbo[u] + q * cells + src[u]);
+#pragma unroll
+  for (int u = 0; u < kVPT; ++u)
+    if (nbo[u] >= 0) *reinterpret_cast<VT *>(base + dst[u]) = v[u];
 }
 
 // ---------------------------------------------------------------- pencil solves
@@ -282,9 +299,9 @@ cfd_status launch_exchange(cfd_blocks_s *B, void *fields, int nf, cudaStream_t s
     auto go = [&](auto tag, auto nc, auto gc, auto vc) {
       using T = decltype(tag);
       constexpr int V = decltype(vc)::value;
-      dim3 grid((unsigned)((ghosts / V + 255) / 256), nblk * nf);
+      dim3 grid((unsigned)((ghosts / V + 256 * kVPT - 1) / (256 * kVPT)), nblk * nf);
       k_exchange<T, decltype(nc)::value, decltype(gc)::value, V><<<grid, 256, 0, st>>>(
-          static_cast<T *>(fields), nf, B->d_groups[gi], N, g, B->d_extpre, B->d_nbr);
+          static_cast<T *>(fields), nf, B->d_groups[gi], B->group_b0[gi], N, g, B->d_exch);
     };
     auto by_size = [&](auto tag, auto vc) {
       using I = std::integral_constant<int, 0>;

@@ -151,6 +151,10 @@ struct cfd_blocks_s {
   // device copies
   int *d_nbr = nullptr;
   long long *d_extpre = nullptr, *d_intpre = nullptr;
+  // ghost exchange: per block its 26 neighbours' field offsets (extpre of the neighbour, -1 for
+  // none) and its own (entry 26), so a copy needs one table load
+  long long *d_exch = nullptr;
+  std::vector<int> group_b0;           // per group: first block id if the group's ids are consecutive, else -1
   double *d_scale = nullptr;
   int *d_nvec = nullptr;
   std::vector<int *> d_groups;
