@@ -1094,6 +1094,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     // unchecked conversion: Y * 2^E (|Y| < 2^55) or a * 2^E (an FP32 accumulator) stays normal
     constexpr int kExLo = sizeof(TO) == 8 ? (TFM ? -870 : -1022) : -126;
     constexpr int kExHi = sizeof(TO) == 8 ? (TFM ? 1000 : 969) : 127;
+    // launch-invariant: this thread's rows of a pass, their segment, and per pass the segment's
+    // mode and output slot
+    const int RH = R / 2, r0 = ehalf * RH;  // the two warps of a quadrant split the rows
+    const int sg = r0 / P.seg_rows, i0 = r0 - sg * P.seg_rows;
+    const int mode0 = P.seg_mode[0][sg], mode1 = P.passes > 1 ? P.seg_mode[1][sg] : -1;
+    const long long opoff0 = (long long)P.seg_op[0][sg] * n3,
+                    opoff1 = P.passes > 1 ? (long long)P.seg_op[1][sg] * n3 : 0;
     int it = 0, pit = 0;
     const TileRange tr = tile_range(P);
     for (int tile = tr.first; tile < tr.end && !failed; tile += tr.step, ++it) {
@@ -1103,41 +1110,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       const int etau = s_etau[(it & 7) * kTile + pl];
       const bool bad = etau == kBadTau;
       const int ebase = TFM ? etau : etau - 14 - 8 * L;
+      // per tile: the output and intermediate addresses of this thread's pencil (the pass adds
+      // its operator's output slot)
+      TO *fb_tile = static_cast<TO *>(P.out);
+      if (interior)
+        fb_tile += (long long)P.nf * P.nops * (P.contig ? P.int0 + (long long)c.lb * n3 : P.intpre[c.b]) +
+                   (long long)c.q * P.nops * n3 + (long long)(c.t1 - P.int_lo1) * f_t1 +
+                   (long long)(c.t2 - P.int_lo2) * f_t2;
+      double *sb = P.scratch_out;
+      const bool any_sc = sb != nullptr && c.valid;
+      if (any_sc)
+        sb += ((long long)(P.sc_local ? P.sc_local[c.lb] : c.lb) * P.nf + c.q) * (long long)P.sc_box +
+              (long long)(sc_s1 + c.t1) * c_t1 + (long long)(sc_s2 + c.t2) * c_t2;
+      const long long sstr = c_ax;
+      // interior pencils near an x (y) face also fill the neighbour's ghost column (row)
+      double *gx = nullptr, *gyp = nullptr;
+      if (any_sc && P.ghost_x) {
+        const int xs = sc_s2 + c.t2;  // t2 is the x axis in the stages that write intermediates
+        const long long jump = (long long)P.nf * (long long)P.sc_box;
+        // (no write where the block has no such neighbour: it computes that strip itself)
+        const int *nl = P.nl + c.lb * 4;
+        if (xs < 2 * g) { if (nl[0] >= 0) gx = sb + (long long)(nl[0] - c.lb) * jump + N; }
+        else if (xs >= N) { if (nl[1] >= 0) gx = sb + (long long)(nl[1] - c.lb) * jump - N; }
+        if (P.ghost_y) {
+          const int ys = sc_s1 + c.t1;  // t1 is the y axis (z stage)
+          if (ys < 2 * g) { if (nl[2] >= 0) gyp = sb + (long long)(nl[2] - c.lb) * jump + (long long)N * ss1; }
+          else if (ys >= N) { if (nl[3] >= 0) gyp = sb + (long long)(nl[3] - c.lb) * jump - (long long)N * ss1; }
+        }
+      }
       for (int ps = 0; ps < P.passes; ++ps, ++pit) {
         const int tb = pit % kPassBufs, tuse = pit / kPassBufs;
         if (!mbar_wait_bounded(t_full(tb), (uint32_t)(tuse & 1), WL)) { failed = true; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int RH = R / 2, r0 = ehalf * RH;  // the two warps of a quadrant split the rows
-        const int sg = r0 / P.seg_rows, i0 = r0 - sg * P.seg_rows;
-        const int mode = P.seg_mode[ps][sg];
+        const int mode = ps ? mode1 : mode0;
         const bool wf = (mode == 0 || mode == 3) && interior;
         const bool ws = (mode == 2 || mode == 3) && c.valid;
-        TO *fb = static_cast<TO *>(P.out);
-        double *sb = P.scratch_out;
-        if (wf)
-          fb += (long long)P.nf * P.nops * (P.contig ? P.int0 + (long long)c.lb * n3 : P.intpre[c.b]) +
-                ((long long)c.q * P.nops + P.seg_op[ps][sg]) * n3 +
-                (long long)(c.t1 - P.int_lo1) * f_t1 + (long long)(c.t2 - P.int_lo2) * f_t2;
-        if (ws)
-          sb += ((long long)(P.sc_local ? P.sc_local[c.lb] : c.lb) * P.nf + c.q) * (long long)P.sc_box +
-                (long long)(sc_s1 + c.t1) * c_t1 +
-                (long long)(sc_s2 + c.t2) * c_t2;
-        const long long sstr = c_ax;
-        // interior pencils near an x (y) face also fill the neighbour's ghost column (row)
-        double *gx = nullptr, *gyp = nullptr;
-        if (ws && P.ghost_x) {
-          const int xs = sc_s2 + c.t2;  // t2 is the x axis in the stages that write intermediates
-          const long long jump = (long long)P.nf * (long long)P.sc_box;
-          // (no write where the block has no such neighbour: it computes that strip itself)
-          const int *nl = P.nl + c.lb * 4;
-          if (xs < 2 * g) { if (nl[0] >= 0) gx = sb + (long long)(nl[0] - c.lb) * jump + N; }
-          else if (xs >= N) { if (nl[1] >= 0) gx = sb + (long long)(nl[1] - c.lb) * jump - N; }
-          if (P.ghost_y) {
-            const int ys = sc_s1 + c.t1;  // t1 is the y axis (z stage)
-            if (ys < 2 * g) { if (nl[2] >= 0) gyp = sb + (long long)(nl[2] - c.lb) * jump + (long long)N * ss1; }
-            else if (ys >= N) { if (nl[3] >= 0) gyp = sb + (long long)(nl[3] - c.lb) * jump - (long long)N * ss1; }
-          }
-        }
+        TO *fb = fb_tile + (ps ? opoff1 : opoff0);
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kPassCols + r0);
         const int *rexp = s_rowexp + ps * 48 + r0;
         // rows in groups of 8 (fewer live registers); the pass buffer is released after the last group.
