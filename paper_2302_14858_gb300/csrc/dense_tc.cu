@@ -1899,6 +1899,7 @@ cfd_status dense_apply(cfd_blocks_s *B, const void *fields, int nf, unsigned mas
       P.n2 = N;
       P.int_lo1 = 0; P.int_hi1 = N; P.int_lo2 = 0; P.int_hi2 = N;
       set_segments(P, box, 0, op, -1, -1);
+      P.halo_deg_mask = 1;  // the mixed products apply the degree-1 operator only
       return run_stage(P, box);
     };
     if (odxy >= 0 && (s = scratch_stage(gy, N, N, E, 2, 0, 1, 0, 0, odxy)) != CFD_OK) return s;

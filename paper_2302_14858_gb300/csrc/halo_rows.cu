@@ -114,9 +114,10 @@ __device__ __forceinline__ double hr_result(float sh, float sl, int U) {
   return ldexp(d, U);
 }
 
-// The four rows applied to one pencil: element j of the pencil is load(j), j < E, then the
-// four halo columns hv; coefficients (h, l) per column from shared memory.
-template <typename TI, typename Load>
+// The rows applied to one pencil: element j of the pencil is load(j), j < E, then the four halo
+// columns hv; coefficients (h, l) per column from shared memory.  NR = 4: both degrees; NR = 2:
+// the degree-1 rows only (rows 2 and 3 are written as zero).
+template <typename TI, int NR, typename Load>
 __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4], bool with_halo,
                                         const float4 *ch4, const float4 *cl4, double *o) {
   int U = kZeroExp;
@@ -127,7 +128,7 @@ __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4],
   if (U == kBadExp || U == kZeroExp) {
     const double v = U == kBadExp ? __longlong_as_double(0x7FF8000000000000ll) : 0.0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) o[r] = v;
+    for (int r = 0; r < 4; ++r) o[r] = r < NR ? v : 0.0;
     return;
   }
   float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
@@ -139,8 +140,10 @@ __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4],
     const float4 ch = ch4[j], cl = cl4[j];
     hr_acc<LOW>(sh[0], sl[0], ch.x, cl.x, fh, fl);
     hr_acc<LOW>(sh[1], sl[1], ch.y, cl.y, fh, fl);
-    hr_acc<LOW>(sh[2], sl[2], ch.z, cl.z, fh, fl);
-    hr_acc<LOW>(sh[3], sl[3], ch.w, cl.w, fh, fl);
+    if constexpr (NR == 4) {
+      hr_acc<LOW>(sh[2], sl[2], ch.z, cl.z, fh, fl);
+      hr_acc<LOW>(sh[3], sl[3], ch.w, cl.w, fh, fl);
+    }
   }
   if (with_halo) {
 #pragma unroll
@@ -150,12 +153,14 @@ __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4],
       const float4 ch = ch4[E + m], cl = cl4[E + m];
       hr_acc<true>(sh[0], sl[0], ch.x, cl.x, fh, fl);
       hr_acc<true>(sh[1], sl[1], ch.y, cl.y, fh, fl);
-      hr_acc<true>(sh[2], sl[2], ch.z, cl.z, fh, fl);
-      hr_acc<true>(sh[3], sl[3], ch.w, cl.w, fh, fl);
+      if constexpr (NR == 4) {
+        hr_acc<true>(sh[2], sl[2], ch.z, cl.z, fh, fl);
+        hr_acc<true>(sh[3], sl[3], ch.w, cl.w, fh, fl);
+      }
     }
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) o[r] = hr_result(sh[r], sl[r], U);
+  for (int r = 0; r < 4; ++r) o[r] = r < NR ? hr_result(sh[r], sl[r], U) : 0.0;
 }
 
 // One thread per pencil, 128 threads per CTA.  Each warp first stages its 32 pencils in
@@ -165,7 +170,7 @@ __device__ __forceinline__ void hr_rows(Load load, int E, const double (&hv)[4],
 // consecutive elements of the warp's rows.  Then each lane works on its row from there.
 constexpr int kHaloThreads = 128;
 
-template <typename TI>
+template <typename TI, int NR>
 __global__ void __launch_bounds__(kHaloThreads) k_halo_rows(const __grid_constant__ DenseParams P,
                                                             const __grid_constant__ HaloRows R) {
   extern __shared__ __align__(16) unsigned char hr_smem[];
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(kHaloThreads) k_halo_rows(const __grid_constan
   }
   double *o = P.halo_out + (((long long)b * P.nf + q) * np + p) * 4;
   const TI *row = tile + lane * (E + 1);
-  hr_rows<TI>([&](int j) { return row[j]; }, E, hv, P.halo_in != nullptr, s_ch, s_cl, o);
+  hr_rows<TI, NR>([&](int j) { return row[j]; }, E, hv, P.halo_in != nullptr, s_ch, s_cl, o);
 }
 
 }  // namespace
@@ -245,8 +250,16 @@ cfd_status halo_rows_launch(const DenseParams &P, const HaloRows &R, bool f32_in
   // pencils staged in shared memory: 4 warps x 32 pencils x (E + 1) values (<= 46 KB)
   const size_t smem = (size_t)(kHaloThreads / 32) * 32 * (E + 1) * (f32_in ? 4 : 8);
   launch_begin(KF_HALO, st);
-  if (f32_in) k_halo_rows<float><<<grid, kHaloThreads, smem, st>>>(P, R);
-  else k_halo_rows<double><<<grid, kHaloThreads, smem, st>>>(P, R);
+  // a stage whose final pass reads only the degree-1 halo values (halo_deg_mask 1: the T stages
+  // of the mixed derivatives) needs rows 0 and 1 only
+  const bool deg1 = P.halo_deg_mask == 1;
+  if (f32_in) {
+    if (deg1) k_halo_rows<float, 2><<<grid, kHaloThreads, smem, st>>>(P, R);
+    else k_halo_rows<float, 4><<<grid, kHaloThreads, smem, st>>>(P, R);
+  } else {
+    if (deg1) k_halo_rows<double, 2><<<grid, kHaloThreads, smem, st>>>(P, R);
+    else k_halo_rows<double, 4><<<grid, kHaloThreads, smem, st>>>(P, R);
+  }
   launch_end(KF_HALO, st);
   return cuda_fail(cudaGetLastError(), "k_halo_rows launch");
 }
