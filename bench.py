@@ -268,8 +268,9 @@ def _eval_torch(f, X, Y, Z, torch):
 # ------------------------------------------------------------------ algorithmic work
 
 
-def banded_flops_per_step(mesh, nf, mask_ops, n_iter, M=3, h=4, g=4):
-    """FP64 flops of the banded path (RHS FMA chains + Thomas sweeps) for one apply."""
+def banded_flops_per_step(mesh, nf, mask_ops, n_iter, M=3, h=4, g=4, orders=2):
+    """FP64 flops of the banded path (RHS FMA chains + Thomas sweeps) for one apply; a mixed
+    derivative is solved in ``orders`` orders (2: both, averaged; 1: one order)."""
     def closed(N, pencils):
         rows_int, rows_clo = N - 2, 2
         rhs = rows_int * (2 * (2 * M + 1) - 1) + rows_clo * (2 * (2 * h + 1) - 1)
@@ -290,7 +291,7 @@ def banded_flops_per_step(mesh, nf, mask_ops, n_iter, M=3, h=4, g=4):
             if len(op) == 2 or op[1] == op[2]:
                 total += stage(N, N * N)
             else:
-                total += 2 * (stage(N, E * N) + stage(N, N * N)) + 2 * N ** 3
+                total += orders * (stage(N, E * N) + stage(N, N * N)) + (2 * N ** 3 if orders == 2 else 0)
     return total * nf
 
 
@@ -816,17 +817,33 @@ def main():
             cfd.cfd_exchange_ghosts(blocks, fields, nf, stream)
             cfd.cfd_apply(blocks, fields, nf, mask, cfd.CFD_FP64_BANDED, n_iter, ref, work, stream)
 
+        def line_roofline(orders):
+            # k_line alone, per-launch CUDA events over a few more steps (FP64-pipe bound)
+            cfd.cfd_profile_enable(True)
+            torch.cuda.synchronize()
+            ms = timed(step64, args.compare_steps, stream, torch)
+            nl, tl = cfd.cfd_profile_read(cfd.KERNEL_FAMILIES["line"])
+            cfd.cfd_profile_enable(False)
+            fl = banded_flops_per_step(mesh, nf, op_names, n_iter, orders=orders) * args.compare_steps
+            ach = fl / (tl * 1e-3) / 1e9
+            return {"kernel": "k_line (FP64 banded pencil solve)", "bound": "alu", "achieved": round(ach, 1),
+                    "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s", "frac": round(ach / FP64_NOMINAL_GFLOPS, 4),
+                    "launches_per_step": nl / args.compare_steps, "avg_launch_ms": round(tl / max(nl, 1), 5),
+                    "share_of_step": round(tl / (ms * args.compare_steps), 4)}
+
         step64()
         torch.cuda.synchronize()
         ms64 = timed(step64, args.compare_steps, stream, torch)
+        roof64 = line_roofline(2)
         one_order = blocks.handle is not None and nops == 9
-        ms64_one = None
+        ms64_one = roof64_one = None
         if one_order:
             try:
                 cfd.cfd_blocks_set_mixed_order(blocks, True)
                 step64()
                 torch.cuda.synchronize()
                 ms64_one = timed(step64, args.compare_steps, stream, torch)
+                roof64_one = line_roofline(1)
             except cfd.CfdError:
                 ms64_one = None
             cfd.cfd_blocks_set_mixed_order(blocks, False)
@@ -838,9 +855,10 @@ def main():
         worst = float(rel.max())
         base_ms = ms64_one if ms64_one else ms64
         compare = {"fp64_banded": {"value": round(units / (ms64 * 1e-3) / 1e9, 4), "ms_per_step": round(ms64, 4),
-                                   "mixed": "symmetrised (both orders averaged)"},
+                                   "mixed": "symmetrised (both orders averaged)", "roofline": roof64},
                    "fp64_banded_one_order": ({"value": round(units / (ms64_one * 1e-3) / 1e9, 4),
-                                              "ms_per_step": round(ms64_one, 4), "mixed": "one order"}
+                                              "ms_per_step": round(ms64_one, 4), "mixed": "one order",
+                                              "roofline": roof64_one}
                                              if ms64_one else None),
                    "speedup_vs_fp64_banded": round(base_ms / ms_step, 3),
                    "speedup_basis": "one-order FP64 banded (equal work)" if ms64_one else "FP64 banded",

@@ -699,7 +699,12 @@ __device__ __forceinline__ TileCoord tile_coord(const DenseParams &P, int tile, 
 // ITER = 1: the final pass of an iterated stage (halo_in set), whose TMA-staged tiles take the
 // neighbours' previous iterate as 4 extra columns.  A separate instantiation keeps that code out
 // of the closed passes' producer loop (measured 5 % slower with it there).
-template <typename TI, typename TO, int KP, int S, int L, int TFM, bool ITER>
+//
+// SPL = 1: a closed pass whose pencils fill an odd number of 8-value K chunks (E = N + 8 for
+// N = 16, 32), the last chunk all padding.  The two producer threads of a pencil then split
+// the last real chunk four values each instead of one of them taking it whole, so both do the
+// same digit work.
+template <typename TI, typename TO, int KP, int S, int L, int TFM, bool ITER, bool SPL>
 __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ DenseParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int EB = TFM ? 4 : 2;  // bytes per operand element (TF32 or BF16)
@@ -795,6 +800,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
     // kParts threads per pencil; part `half` splits K chunks half, half + kParts, ...
     const int pl = (warp & 3) * 32 + lane, half = warp >> 2;
     constexpr int CPP = (NCH + kParts - 1) / kParts;  // K chunks per producer thread
+    static_assert(!SPL || (!TFM && !ITER && kParts == 2 && NCH % 2 == 0), "split last chunk: two threads per pencil");
     const float inv_n2 = 1.0f / (float)P.n2;
     const int cpr = E / VE;  // 16-byte chunks per pencil row (x axis); E * sizeof(TI) is a multiple of 16
     const float inv_cpr = 1.0f / (float)cpr;
@@ -934,9 +940,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       const int kv = c.valid ? P.kext : 0;  // values of this pencil (none for a pencil past the end)
 #pragma unroll
       for (int h = 0; h < CPP; ++h) {
+        // the last slot of a split pass: values 4 half .. 4 half + 3 of chunk NCH - 2
+        const bool sl = SPL && h == CPP - 1;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int j = (half + kParts * h) * 8 + k;
+        for (int k = 0; k < (sl ? 4 : 8); ++k) {
+          const int j = sl ? (NCH - 2) * 8 + 4 * half + k : (half + kParts * h) * 8 + k;
           v[h][k] = j < kv ? stg[stg_index(j)] : TI(0);
           em = max(em, biased_exp(v[h][k]));
         }
@@ -980,6 +988,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense(const __grid_constant__ D
       } else {
 #pragma unroll
       for (int h = 0; h < CPP; ++h) {
+        if (SPL && h == CPP - 1) {
+          // half of chunk NCH - 2 (8-byte digit stores); the second thread also writes the
+          // zero digits of the padding chunk NCH - 1
+          uint32_t w2[S][2];
+#pragma unroll
+          for (int k = 0; k < 4; k += 2) {
+            uint32_t d0[S], d1[S];
+            digits_of<S>(fixed_of(v[h][k], emax), d0);
+            digits_of<S>(fixed_of(v[h][k + 1], emax), d1);
+#pragma unroll
+            for (int t = 0; t < S; ++t) w2[t][k / 2] = __byte_perm(d0[t], d1[t], 0x7632);
+          }
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            uint16_t *row = Ab + (size_t)t * kTile * KP + (size_t)row_group * NCH * 64 + row_in * 8;
+            *reinterpret_cast<uint2 *>(row + (NCH - 2) * 64 + 4 * half) = make_uint2(w2[t][0], w2[t][1]);
+            if (half) *reinterpret_cast<uint4 *>(row + (NCH - 1) * 64) = make_uint4(0u, 0u, 0u, 0u);
+          }
+          continue;
+        }
         const int ch = half + kParts * h;
         if (ch >= NCH) break;
         uint32_t w[S][4];
@@ -1212,15 +1240,21 @@ template <typename TI, typename TO, int KP>
 cfd_status launch_kp(const DenseParams &P, int S, int L, size_t smem, unsigned grid, cudaStream_t st) {
   void (*fn)(const __grid_constant__ DenseParams);
   const bool it = P.halo_in != nullptr;
-  if (S == 5 && L == 4) fn = it ? k_dense<TI, TO, KP, 5, 4, 0, true> : k_dense<TI, TO, KP, 5, 4, 0, false>;
-  else if (S == 2 && L == 1) fn = it ? k_dense<TI, TO, KP, 2, 1, 0, true> : k_dense<TI, TO, KP, 2, 1, 0, false>;
-  else if (S == 1 && L == 0) fn = it ? k_dense<TI, TO, KP, 1, 0, 1, true> : k_dense<TI, TO, KP, 1, 0, 1, false>;
+  // the exact slices' closed passes whose last K chunk is all padding split the last real one,
+  // except in the stages that also write an intermediate (measured 1-3 % slower there, 3 %
+  // faster in the others)
+  const bool spl = !it && P.scratch_out == nullptr && P.kext > KP - 16 && P.kext <= KP - 8;
+  if (S == 5 && L == 4)
+    fn = it ? k_dense<TI, TO, KP, 5, 4, 0, true, false>
+            : (spl ? k_dense<TI, TO, KP, 5, 4, 0, false, true> : k_dense<TI, TO, KP, 5, 4, 0, false, false>);
+  else if (S == 2 && L == 1) fn = it ? k_dense<TI, TO, KP, 2, 1, 0, true, false> : k_dense<TI, TO, KP, 2, 1, 0, false, false>;
+  else if (S == 1 && L == 0) fn = it ? k_dense<TI, TO, KP, 1, 0, 1, true, false> : k_dense<TI, TO, KP, 1, 0, 1, false, false>;
   else { set_error("dense: unsupported slice configuration"); return CFD_ERR_UNSUPPORTED; }
   // The shared-memory opt-in is set once per device and instantiation (and raised when a
   // launch needs more), so that later calls issue nothing but the launch: a stream being
   // captured into a CUDA graph sees only kernel nodes.
-  static size_t opted[6][64] = {};  // [slice configuration, iterated][device]
-  const int v = (S == 5 ? 0 : (S == 2 ? 1 : 2)) + (it ? 3 : 0);
+  static size_t opted[7][64] = {};  // [slice configuration, iterated or split][device]
+  const int v = (S == 5 ? 0 : (S == 2 ? 1 : 2)) + (it ? 3 : 0) + (S == 5 && spl ? 6 : 0);
   int dev = 0;
   cfd_status s = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
   if (s != CFD_OK) return s;
