@@ -92,7 +92,7 @@ DEFAULT_WORKLOAD = "cfd256_b32_f4_fp64"
 MEASURED_TRAFFIC = {
     # 256^3 as 512 blocks of 32^3, 4 FP64 fields, 9 ops: one-pass capture of the 6 k_dense
     # launches of a step at full size (profiles/k_dense_tc_exact_cfd128_b32_f4.md)
-    ("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1756705443,
+    ("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1757165301,
 }
 
 
