@@ -93,6 +93,9 @@ MEASURED_TRAFFIC = {
     # 256^3 as 512 blocks of 32^3, 4 FP64 fields, 9 ops: one-pass capture of the 6 k_dense
     # launches of a step at full size (profiles/k_dense_tc_exact_cfd128_b32_f4.md)
     ("cfd256_b32_f4_fp64", "tc_bf16_exact", 0): 1757165301,
+    # 448 x 16^3 + 64 x 32^3, 22 FP32 fields, 9 ops: one-pass capture of the 24 k_dense launches
+    # of a step at full size (profiles/launches_box448x16_64x32_f22_fp32_tc_exact.md)
+    ("box448x16_64x32_f22_fp32", "tc_bf16_exact", 0): 415090976,
 }
 
 
